@@ -1,0 +1,89 @@
+"""The pins have teeth: copies of the oracle with one planted mistake each fail them.
+
+Each plant (ORACLE_PLANT=k in oracle/wigner_oracle.c, built into a separate
+library on the CPU) is a plausible slip: a dropped d^{l-1} term, a lost seed
+sign, cos for sin in the seed, a coefficient one order off, a pair not
+rescaled jointly, an unconjugated beam, a wrong beam column.  The battery below
+re-runs a compact version of the pins; the real oracle passes every check and
+every planted copy fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1002_1050_gb300.inputs import beta_gauss_legendre, sky_alm
+from wigner_exact import d_jacobi_mp, d_mp
+
+BETAS = np.array([0.3, 1.2, 2.2, 2.9])
+
+
+def _small_exact(orc):
+    L = 6
+    d = orc.d_table(L, L, L, BETAS)
+    for j, b in enumerate(BETAS):
+        for m in range(L + 1):
+            for mp in range(L + 1):
+                for l in range(max(m, mp), L + 1):
+                    if abs(d[m, mp, l, j] - float(d_mp(l, m, mp, float(b), 30))) > 1e-13:
+                        return False
+    return True
+
+
+def _long_scaled_chain(orc):
+    for (l, m, mp, b) in [(2000, 2, 1500, 0.6), (3000, 3, 1500, 2.6)]:
+        want = float(d_jacobi_mp(l, m, mp, b, 30))
+        got = orc.d_single(l, m, mp, b)
+        if abs(want - got) > 1e-10 * max(1.0, abs(want)):
+            return False
+    return True
+
+
+def _complex_beam():
+    L, MB, MS = 30, 3, 10
+    rng = np.random.default_rng(1)
+    a = sky_alm(L, MS, 2)
+    b = rng.standard_normal((L + 1, MB + 1)) + 1j * rng.standard_normal((L + 1, MB + 1))
+    b[np.arange(MB + 1)[None, :] > np.arange(L + 1)[:, None]] = 0
+    return L, MB, MS, a, b
+
+
+def _conv_beta_zero(orc):
+    L, MB, MS, a, b = _complex_beam()
+    C = orc.conv_sum(L, MB, MS, np.array([0.0]), a, b)
+    for mb in range(MB + 1):
+        for ms in range(MS + 1):
+            want = np.sum(np.conj(b[mb:, mb]) * a[mb:, ms]) if mb == ms else 0.0
+            if abs(C[mb, ms, 0] - want) > 1e-12:
+                return False
+    return True
+
+
+def _conv_gl_projection(orc):
+    L, MB, MS, a, b = _complex_beam()
+    beta, W = beta_gauss_legendre(L + 1)
+    C = orc.conv_sum(L, MB, MS, beta, a, b)
+    d = O.d_table(L, MB, MS, beta)  # the real oracle's d-table, pinned separately
+    for mb in range(MB + 1):
+        for ms in range(MS + 1):
+            proj = d[mb, ms] @ (W * C[mb, ms])
+            want = np.array([2.0 / (2 * l + 1) * np.conj(b[l, mb]) * a[l, ms] if l >= max(mb, ms) else 0.0
+                             for l in range(L + 1)])
+            if np.max(np.abs(proj - want)) > 1e-12:
+                return False
+    return True
+
+
+BATTERY = [_small_exact, _long_scaled_chain, _conv_beta_zero, _conv_gl_projection]
+
+
+def test_real_oracle_passes_battery():
+    for chk in BATTERY:
+        assert chk(O), chk.__name__
+
+
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7])
+def test_planted_mistake_is_caught(plant):
+    orc = O.Planted(plant)
+    assert not all(chk(orc) for chk in BATTERY), f"plant {plant} slipped through every pin"
