@@ -1,0 +1,366 @@
+"""Benchmark of the fused FP64 recursion + l-sum on GB300.
+
+One step = one wigner_conv_sum call over the whole workload (every chain runs the
+seed, the scaled/plain l-recursion and the weighted sum): L = 4096, m_b <= 8,
+m_sky <= 4096, 2048 Gauss-Legendre angles, seeded sky/beam (synthetic stand-ins for
+the Planck inputs of Sec. 4.4).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one process per GPU): each rank takes its own 2048-angle slice of a
+2048*N-node Gauss-Legendre grid (independent angles, no collective), so the work per
+GPU is fixed and the reported value is the whole job's evaluations per second.
+--impl reference times the CPU oracle on this host's cores (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "d^l_{mm'} evals/s and conv-sum GFLOP/s vs FMA peak, FP32 vs FP64 at stated error"
+WORKLOAD = "conv_fp64_l4096"
+L_MAX, MB_MAX, MS_MAX, N_BETA = 4096, 8, 4096, 2048
+# FP64 FMA throughput of the GB300 SM: 2 lanes/clock/SM (nominal 1.25 TFLOP/s at the
+# 2070 MHz maximum clock: 152 SMs * 2 FMA * 2 flop * 2.07e9 = 1.259e12 flop/s)
+SMS, FP64_FMA_PER_CLK_SM, SM_MAX_MHZ = 152, 2, 2070.0
+FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(rank: int, world: int):
+    """(beta, a, b) of this rank: its contiguous slice of a 2048*world-node GL grid."""
+    from paper_1002_1050_gb300 import inputs as I
+
+    nb_total = N_BETA * world
+    beta = I.beta_gauss_legendre(nb_total)[0][rank * N_BETA:(rank + 1) * N_BETA]
+    a = I.sky_alm(L_MAX, MS_MAX, 0)
+    b = I.beam_blm(L_MAX, MB_MAX)
+    return np.ascontiguousarray(beta), a, b
+
+
+def _elements(n_beta: int) -> int:
+    from paper_1002_1050_gb300 import inputs as I
+
+    return I.n_elements(L_MAX, MB_MAX, MS_MAX, n_beta)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples of this process's GPU during the timed region."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                if self.uuid and parts[0] != self.uuid:
+                    continue
+                try:
+                    sm.append(float(parts[1].split()[0]))
+                    smax.append(float(parts[2].split()[0]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _oracle_sample(beta, a, b, n_sample: int):
+    """Oracle on a bounded sample: n_sample angles evenly spread over the rank's grid, all columns."""
+    from oracle import oracle as O
+
+    sel = np.linspace(0, beta.size - 1, n_sample).round().astype(int)
+    bs = np.ascontiguousarray(beta[sel])
+    t0 = time.perf_counter()
+    O.conv_sum(L_MAX, MB_MAX, MS_MAX, bs, a, b)
+    dt = time.perf_counter() - t0
+    return _elements(n_sample), dt, O.num_threads()
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    beta, a, b = _workload(0, 1)
+    n_sample = args.ref_sample
+    for _ in range(args.warmup):
+        _oracle_sample(beta, a, b, max(1, n_sample // 4))
+    elems, times, cores = 0, [], 1
+    for _ in range(args.steps):
+        e, dt, cores = _oracle_sample(beta, a, b, n_sample)
+        elems += e
+        times.append(dt)
+    tot = sum(times)
+    value = elems / tot
+    sample = f"{n_sample} of {N_BETA} angles per step, all {(MB_MAX + 1) * (MS_MAX + 1)} chain columns"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"{WORKLOAD} (L=4096, m_b<=8, m_sky<=4096, 2048 GL angles)",
+                                        "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl", device_id=dev)
+        dist = dist_mod
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1002_1050_gb300 import wigner as W
+
+    beta_h, a_h, b_h = _workload(rank, world)
+    beta = torch.from_numpy(beta_h).to(dev)
+    a = torch.from_numpy(a_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    out = torch.empty((MB_MAX + 1, MS_MAX + 1, beta.numel()), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    elems_rank = _elements(beta.numel())
+
+    # algorithmic flop count (5 per recursion element + 4 per summed element), untimed
+    cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+    W.wigner_conv_sum(beta, a, b, out=out, counters=cnt)
+    W.check_device_status()
+    n_elem, n_sum = int(cnt[0]), int(cnt[1])
+    assert n_elem == elems_rank, (n_elem, elems_rank)
+    flops_launch = 5 * n_elem + 4 * n_sum
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        W.wigner_conv_sum(beta, a, b, out=out)
+    torch.cuda.synchronize()
+    W.check_device_status()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            W.wigner_conv_sum(beta, a, b, out=out)
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    W.check_device_status()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [s.elapsed_time(e) for s, e in ev]
+    clocks = clk.summary()
+
+    # whole-job time = max over ranks
+    t_all = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    total_ms = float(t_all.item())
+    value = elems_rank * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public call with host buffers: H2D inputs (pinned), kernel, D2H result
+    beta_p = torch.from_numpy(beta_h).pin_memory()
+    a_p = torch.from_numpy(a_h).pin_memory()
+    b_p = torch.from_numpy(b_h).pin_memory()
+    c_p = torch.empty(out.shape, dtype=torch.complex128).pin_memory()
+    h2d = beta_p.numel() * 8 + a_p.numel() * 16 + b_p.numel() * 16
+    d2h = c_p.numel() * 16
+
+    def e2e_step():
+        bd = beta_p.to(dev, non_blocking=True)
+        ad = a_p.to(dev, non_blocking=True)
+        bbd = b_p.to(dev, non_blocking=True)
+        W.wigner_conv_sum(bd, ad, bbd, out=out)
+        c_p.copy_(out, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 5))
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_value = elems_rank * world * e2e_steps / (float(e2e_ms.item()) / 1e3)
+
+    # FMA-pipe microbenchmark (measured FP64 FMA throughput, for context)
+    peak_meas = None
+    try:
+        blocks, threads, iters = SMS * 8, 256, 4000
+        W.wigner_fma_peak(0, blocks, threads, 200)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        _, ops = W.wigner_fma_peak(0, blocks, threads, iters)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        peak_meas = 2.0 * ops / (p0.elapsed_time(p1) / 1e3) / 1e12
+    except Exception:
+        pass
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    mean_launch_ms = float(np.mean(launch_ms))
+    achieved = flops_launch / (mean_launch_ms / 1e3) / 1e12
+    traffic = _profile_traffic()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        e, dt, cores = _oracle_sample(beta_h, a_h, b_h, args.cpu_sample)
+        cpu = {"value": e / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample} of {N_BETA} angles, all {(MB_MAX + 1) * (MS_MAX + 1)} chain columns "
+                         f"({e:.3e} elements, {dt:.1f} s)"}
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} (L=4096, m_b<=8, m_sky<=4096, 2048 Gauss-Legendre angles per GPU, "
+                               "seeded sky C_l=1/(l+10)^2, elliptical Gaussian beam FWHM 0.01 e=0.2)",
+                   "form": "fp64", "elements_per_step": elems_rank * world,
+                   "l2": "inputs (a: 268 MB) and output (C: 1.21 GB) larger than L2 (129 MB)"},
+        "gflops_algorithmic": flops_launch * world / (total_ms / args.steps / 1e3) / 1e9,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "conv_fp64_kernel",
+                     "flops_per_launch": flops_launch, "summed_elements": n_sum, "elements": n_elem,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                     "fma_microbench_tflops": peak_meas},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "conv_fp64_l4096_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("bytes_per_launch")
+    except Exception:
+        return None
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--cpu-sample", type=int, default=48, help="angles in the oracle's CPU-baseline sample")
+    p.add_argument("--ref-sample", type=int, default=8, help="angles per step in the reference arm")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--n-beta", type=int, default=N_BETA,
+                   help="angles per GPU (default 2048; smaller only for profiling captures)")
+    args = p.parse_args(argv)
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    global N_BETA
+    N_BETA = args.n_beta
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

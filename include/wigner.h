@@ -1,0 +1,180 @@
+/*
+ * wigner.h -- C ABI of the GB300 (sm_103a) library for reduced Wigner matrices
+ * d^l_{m_b m_sky}(beta) and the beam-convolution l-sum of Prezeau & Reinecke,
+ * "Algorithm for the evaluation of reduced Wigner matrices".
+ *
+ * What is computed
+ *   d^l_{m m'}(beta) = <l m| exp(-i beta J_y) |l m'>            (Sec. 2, Eq. reducedwignerdef)
+ *   by the stable l-recursion (Sec. 2, Eq. lrec; Sec. 4.2.2 table form)
+ *       d^{l+1} = F0_l (cos beta - F1_l) d^l - F2_l d^{l-1}
+ *   started at l0 = max(m_b, m_sky) from the log-space seeds of Eqs. ini1-ini2 and
+ *   logstart (Sec. 3.2), carried in scaled doubles v = d * 2^(90 n) until the value
+ *   reaches 2^-900 and in plain doubles after that (Sec. 3.2); and the l-sum
+ *       C_{m_b m_sky}(beta) = sum_{l=l0}^{l_max} conj(b_{l m_b}) a_{l m_sky} d^l_{m_b m_sky}(beta)
+ *   of Sec. 4.1, Eq. convdef, fused with the recursion so the d-table is never stored.
+ *   Terms are summed from the first l at which |d| >= 1e-30 (Sec. 4.2.1); smaller
+ *   terms change C by less than 1e-30 * sum |w|.
+ *
+ * Conventions (all calls)
+ *   - Orders: 0 <= m_b <= mb_max <= l_max, 0 <= m_sky <= ms_max <= l_max; l_max <= WG_LMAX.
+ *     Only non-negative orders are computed.
+ *   - Angles: beta[j] in [0, pi], float64, device memory, n_beta >= 0 entries.
+ *     beta = 0 and beta = pi are exact: d(0) = delta_{m m'}, d(pi) = (-1)^(l-m') delta_{m,-m'}.
+ *     An angle outside [0, pi] (or NaN) makes the affected outputs NaN and records
+ *     WG_ERR_ARG in the device status word (see wigner_device_status); the call
+ *     itself cannot see device data and returns WG_OK.
+ *   - Complex numbers are wg_c64 {re, im}, layout-compatible with complex128 /
+ *     torch.complex128.  All arrays are dense, row-major, C-contiguous.
+ *   - Every pointer argument is a DEVICE pointer on the current CUDA device unless
+ *     noted; the caller owns every buffer it passes.  The library owns only its
+ *     per-device constant tables (ln n!, square-root tables) and a status word,
+ *     created on the first call on a device (this first call allocates and
+ *     copies, so make it before any stream capture).
+ *   - Execution is asynchronous and stream-ordered on `stream` (a cudaStream_t;
+ *     NULL = legacy default stream).  Calls never throw; they return WG_OK (0) or
+ *     a negative WG_ERR_* code after validating their arguments on the host.
+ *   - Precision forms: WG_FP64 runs everything in IEEE double.  WG_FP32X runs the
+ *     recursion body in float with an int32 exponent carry and compensated float
+ *     sums, with double for the seeds and for the steps near the double root of
+ *     the recursion (turning point / poles); its error is stated per workload.
+ */
+#ifndef WIGNER_GB300_H
+#define WIGNER_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WG_LMAX 32767 /* largest supported l_max */
+
+typedef struct {
+    double re, im;
+} wg_c64;
+
+typedef enum { WG_FP64 = 0, WG_FP32X = 1 } wg_form;
+
+enum {
+    WG_OK = 0,
+    WG_ERR_ARG = -1,         /* invalid argument (sizes, orders, null or misaligned pointer) */
+    WG_ERR_CUDA = -2,        /* a CUDA runtime call failed (message in wigner_last_error_message) */
+    WG_ERR_ALLOC = -3,       /* device allocation of the library's tables failed */
+    WG_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up (reported by wigner_device_status) */
+    WG_ERR_DEVICE = -5,      /* no usable sm_103 device / kernel image */
+    WG_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+};
+
+/* Optional counters filled by some calls (device pointer, may be NULL):
+ *   [0] elements  -- (chain, l) elements evaluated, l0 <= l <= l_max
+ *   [1] summed    -- elements whose term entered the sum (from the first |d| >= 1e-30 on)
+ * The library ADDS to the counters (atomically); the caller zeroes them. */
+typedef unsigned long long wg_counter;
+
+/* ---------------------------------------------------------------------------
+ * wigner_d_table -- the full table (Sec. 3.2 l-recursion, Eqs. lrec, ini1-ini2, logstart).
+ *   d_out[mb][ms][l][j] = d^l_{mb,ms}(beta_j),  shape (mb_max+1, ms_max+1, l_max+1, n_beta),
+ *   float64, 8-byte aligned; entries with l < max(mb, ms) are written as 0.
+ *   form: WG_FP64 or WG_FP32X (the stored values are double in both cases).
+ *   counters: optional, see above.
+ * Errors: WG_ERR_ARG for bad orders/sizes/pointers; WG_ERR_CUDA on launch failure.
+ * ------------------------------------------------------------------------- */
+int wigner_d_table(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                   wg_form form, double *d_out, wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * wigner_d_table_backward -- adjoint of wigner_d_table with respect to beta.
+ *   grad_beta[j] = sum_{mb,ms,l} grad_d[mb][ms][l][j] * d/dbeta d^l_{mb,ms}(beta_j)
+ *   using Eq. mrec's derivative relation
+ *     d/dbeta d^l_{m m'} = ((m' cos b - m)/sin b) d^l_{m m'} - sqrt((l-m')(l+m'+1)) d^l_{m,m'+1}
+ *   on recomputed chains (the table is not read).  grad_d has d_out's shape and layout.
+ *   grad_beta is OVERWRITTEN (float64[n_beta]).  Angles must be interior (0 < beta < pi);
+ *   at the endpoints the result is NaN and WG_ERR_ARG is recorded in the status word.
+ *   Uses library workspace of (mb_max+1)(ms_max+1) n_beta doubles (grown on demand).
+ * ------------------------------------------------------------------------- */
+int wigner_d_table_backward(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                            const double *grad_d, double *grad_beta, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * wigner_conv_sum -- fused recursion + weighted l-sum (Sec. 4.1 Eq. convdef, Sec. 4.2).
+ *   a: sky coefficients a[l][ms], wg_c64, shape (l_max+1, ms_max+1), 16-byte aligned.
+ *   b: beam coefficients b[l][mb], wg_c64, shape (l_max+1, mb_max+1), 16-byte aligned.
+ *   c_out[mb][ms][j] = sum_{l >= max(mb,ms)} conj(b[l][mb]) a[l][ms] d^l_{mb,ms}(beta_j),
+ *   wg_c64, shape (mb_max+1, ms_max+1, n_beta), overwritten.
+ *   form: WG_FP64 or WG_FP32X.  counters: optional.
+ * ------------------------------------------------------------------------- */
+int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                    const wg_c64 *a, const wg_c64 *b, wg_form form, wg_c64 *c_out,
+                    wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * wigner_conv_sum_backward -- adjoint of wigner_conv_sum for a real loss L, in
+ * PyTorch's convention for complex tensors (grad = dL/dRe + i dL/dIm):
+ *   grad_a[l][ms]  = sum_mb b[l][mb] S[l][mb][ms],      S = sum_j grad_c[mb][ms][j] d^l(beta_j)
+ *   grad_b[l][mb]  = sum_ms a[l][ms] conj(S[l][mb][ms])
+ *   grad_beta[j]   = Re sum_{mb,ms} conj(grad_c) sum_l w_l d/dbeta d^l(beta_j)
+ * with d/dbeta d^l from Eq. mrec's relation (the m_sky+1 neighbour chain), chains
+ * recomputed (no stored table).  c_fwd is the forward result for the same inputs
+ * (used by the beta term); it may be NULL when grad_beta is NULL.
+ * grad_a, grad_b, grad_beta may each be NULL (not computed) and are OVERWRITTEN.
+ * Shapes as in wigner_conv_sum.  FP64 only (form argument reserved: pass WG_FP64).
+ * Uses library workspace of (l_max+1)(mb_max+1)(ms_max+1) complex values.
+ * ------------------------------------------------------------------------- */
+int wigner_conv_sum_backward(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                             const wg_c64 *a, const wg_c64 *b, const wg_c64 *c_fwd,
+                             const wg_c64 *grad_c, wg_c64 *grad_a, wg_c64 *grad_b,
+                             double *grad_beta, wg_form form, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched uneven instances in one persistent launch (Sec. 4.1's per-beta
+ * independence, applied across whole convolutions).  Each instance is one
+ * wigner_conv_sum call; all run in a single kernel launch that pulls work items
+ * (instance, column group, beta chunk) from a queue ordered longest first.
+ * inst: HOST array of n descriptors (device pointers inside).  use_graph != 0
+ * captures the launch into a CUDA graph cached on the plan and replays it.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int l_max, mb_max, ms_max, n_beta;
+    wg_form form;
+    const double *beta;
+    const wg_c64 *a, *b;
+    wg_c64 *c_out;
+} wg_instance;
+
+typedef struct wg_batch_plan wg_batch_plan;
+
+int wigner_batch_plan_create(wg_batch_plan **plan, int n, const wg_instance *inst, int autotune,
+                             void *stream);
+int wigner_batch_run(wg_batch_plan *plan, int use_graph, void *stream);
+void wigner_batch_plan_destroy(wg_batch_plan *plan);
+int wigner_conv_sum_batched(int n, const wg_instance *inst, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Status and diagnostics
+ * ------------------------------------------------------------------------- */
+/* Synchronises `stream`, returns and clears the device status word of the current
+ * device: WG_OK, WG_ERR_ARG (an angle out of range) or WG_ERR_TIMEOUT (a bounded
+ * wait gave up). */
+int wigner_device_status(void *stream);
+const char *wigner_error_string(int code);
+/* Text of the last host-side failure on this thread (empty if none). */
+const char *wigner_last_error_message(void);
+/* Library version and the compute capability it was built for (e.g. 1003 = sm_103). */
+int wigner_version(void);
+int wigner_built_arch(void);
+
+/* ---------------------------------------------------------------------------
+ * FMA-pipe microbenchmark (measures the roofline denominators of the path).
+ *   pipe = 0: FP64 FMA, 1: FP32 FMA.  Runs `iters` iterations of `chains`
+ *   independent FMA chains per thread on blocks x threads; writes a sink value per
+ *   thread to sink (device, blocks*threads doubles) so the work cannot be elided.
+ *   Returns the number of FMA lane-operations performed in *fma_ops (host).
+ * ------------------------------------------------------------------------- */
+int wigner_fma_peak(int pipe, int blocks, int threads, int iters, double *sink,
+                    unsigned long long *fma_ops, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WIGNER_GB300_H */

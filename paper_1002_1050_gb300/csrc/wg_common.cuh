@@ -1,0 +1,245 @@
+// wg_common.cuh -- device-side building blocks shared by the sm_103a kernels.
+//
+//  * double-double arithmetic from the published error-free transforms
+//    (Knuth's TwoSum, Dekker's Fast2Sum, FMA-based TwoProd) for the seeds;
+//  * per-angle quantities of Sec. 4.2.2's first precomputation (cos beta,
+//    ln cos(beta/2), ln sin(beta/2)) evaluated with CUDA's math functions;
+//  * the seed of Eqs. ini1-ini2 / logstart (Sec. 3.2) as a scaled double;
+//  * exponent-field manipulation of doubles (exact multiplication by 2^k for
+//    normal values, done on the integer pipe so the scarce FP64 pipe is left to
+//    the recursion).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wg_internal.h"
+
+namespace wg {
+
+// ---------------------------------------------------------------------------
+// double-double (value = hi + lo, |lo| <= ulp(hi)/2)
+// ---------------------------------------------------------------------------
+struct dd {
+    double hi, lo;
+};
+
+__device__ __forceinline__ dd two_sum(double a, double b) {
+    double s = __dadd_rn(a, b);
+    double bb = __dsub_rn(s, a);
+    double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ dd fast_two_sum(double a, double b) {  // |a| >= |b|
+    double s = __dadd_rn(a, b);
+    double e = __dsub_rn(b, __dsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ dd two_prod(double a, double b) {
+    double p = __dmul_rn(a, b);
+    double e = __fma_rn(a, b, -p);
+    return {p, e};
+}
+
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+    dd s = two_sum(x.hi, y.hi);
+    double e = __dadd_rn(s.lo, __dadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ dd dd_neg(dd x) { return {-x.hi, -x.lo}; }
+
+// x * k for a small integer k (|k| < 2^31): k is exact in double, product via TwoProd
+__device__ __forceinline__ dd dd_mul_d(dd x, double k) {
+    dd p = two_prod(x.hi, k);
+    double e = __fma_rn(x.lo, k, p.lo);
+    return fast_two_sum(p.hi, e);
+}
+
+// ---------------------------------------------------------------------------
+// exponent-field helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int biased_exp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+// x * 2^k for normal x whose result stays normal, by an integer add to the exponent field.
+// Zero stays zero.  (Callers guarantee the range; see the scaled-double invariants.)
+__device__ __forceinline__ double exp_shift(double x, int k) {
+    int hi = __double2hiint(x);
+    int lo = __double2loint(x);
+    int nz = (hi & 0x7fffffff) | lo;
+    hi += (nz != 0) ? (k << 20) : 0;
+    return __hiloint2double(hi, lo);
+}
+
+// 2^k as a double for -1022 <= k <= 1023
+__device__ __forceinline__ double pow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+
+// |x| >= y for y > 0, compared on the bit patterns (integer pipe)
+__device__ __forceinline__ bool abs_ge(double x, long long ybits) {
+    long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+    return b >= ybits;
+}
+
+// ---------------------------------------------------------------------------
+// per-angle quantities (Sec. 4.2.2: cos beta, ln cos(beta/2), ln sin(beta/2))
+// ---------------------------------------------------------------------------
+struct Angle {
+    double cb;    // cos(beta)
+    double sb;    // sin(beta)
+    double lnc;   // ln cos(beta/2)   (unused when c_zero)
+    double lns;   // ln sin(beta/2)   (unused when s_zero)
+    bool c_zero;  // beta == pi
+    bool s_zero;  // beta == 0
+    bool bad;     // beta outside [0, pi] or NaN
+};
+
+__device__ __forceinline__ Angle make_angle(double beta) {
+    Angle t;
+    t.bad = !(beta >= 0.0 && beta <= WG_PI_HI);
+    double b = t.bad ? 1.0 : beta;
+    double s, c;
+    sincos(0.5 * b, &s, &c);
+    t.cb = cos(b);
+    t.sb = sin(b);
+    t.s_zero = (s == 0.0);
+    t.c_zero = (c <= 0.0);
+    // the logarithm of the half-angle factor closer to 1 through log1p(-x^2)/2 keeps
+    // full relative accuracy near the poles
+    t.lnc = (c >= s) ? 0.5 * log1p(-s * s) : log(c);
+    t.lns = (s >= c) ? 0.5 * log1p(-c * c) : log(s);
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// constant tables (device pointers, built once per device on the host)
+// ---------------------------------------------------------------------------
+struct Tables {
+    const double *lnf_hi;  // ln n! = lnf_hi[n] + lnf_lo[n], n <= 2*lcap+1
+    const double *lnf_lo;
+    const double *P;       // P_i = sqrt(1/(i+1)),  i <= 2*lcap+1   (Sec. 4.2.2)
+    const double *Q;       // Q_i = sqrt(i/(i+1))
+    const double *R1;      // 1/(l(l+1)), l >= 1  (R1[0] = 0)
+    const double *R2;      // (l+1)/l,    l >= 1  (R2[0] = 0)
+    int lcap;
+    int *status;           // device status word (WG_DEVERR_* bits)
+};
+
+// ---------------------------------------------------------------------------
+// Seed of a chain (Eqs. ini1-ini2 in log form, Eq. logstart) as a scaled double.
+//   l0 = max(mb, ms), m = min(mb, ms)
+//   ms >= mb : d^{l0}_{mb,l0} = A c^{l0+mb} s^{l0-mb}
+//   mb >  ms : d^{l0}_{l0,ms} = A c^{l0+ms} (-s)^{l0-ms}
+//   ln|d| = (ln (2l0)! - ln (l0+m)! - ln (l0-m)!)/2 + (l0+m) ln c + (l0-m) ln s
+// evaluated in double-double.  Result: value = mant * 2^(90 n); plain (n = 0,
+// mant = the value) when the value is >= 2^-810, else mant in [1, 2^90).
+// ---------------------------------------------------------------------------
+struct Scaled {
+    double mant;
+    int n;
+    bool plain;
+};
+
+__device__ __forceinline__ Scaled seed_value(int mb, int ms, const Angle &t, const Tables &T) {
+    const int l0 = mb > ms ? mb : ms;
+    const int m = mb > ms ? ms : mb;
+    const int p = l0 + m, q = l0 - m;
+    Scaled r;
+    if ((p > 0 && t.c_zero) || (q > 0 && t.s_zero)) {  // a factor is exactly 0 (Sec. 3.2 early stop)
+        r.mant = 0.0;
+        r.n = 0;
+        r.plain = true;
+        return r;
+    }
+    const double sign = (mb > ms && (q & 1)) ? -1.0 : 1.0;
+    dd x = {T.lnf_hi[2 * l0], T.lnf_lo[2 * l0]};
+    x = dd_add(x, dd_neg(dd{T.lnf_hi[p], T.lnf_lo[p]}));
+    x = dd_add(x, dd_neg(dd{T.lnf_hi[q], T.lnf_lo[q]}));
+    x.hi *= 0.5;  // exact
+    x.lo *= 0.5;
+    if (p > 0) x = dd_add(x, dd_mul_d(dd{t.lnc, 0.0}, (double)p));
+    if (q > 0) x = dd_add(x, dd_mul_d(dd{t.lns, 0.0}, (double)q));
+    // split x = k * (90 ln 2) + rem, rem in [0, 90 ln 2)
+    double k = floor(x.hi * WG_INV_LN_S);
+    dd rem = dd_add(x, dd_mul_d(dd{WG_LN_S_HI, 0.0}, -k));  // k * LN_S_HI is exact (|k| < 2^17)
+    rem = dd_add(rem, dd{-k * WG_LN_S_LO, 0.0});
+    if (rem.hi < 0.0) {
+        k -= 1.0;
+        rem = dd_add(dd_add(rem, dd{WG_LN_S_HI, 0.0}), dd{WG_LN_S_LO, 0.0});
+    } else if (rem.hi >= WG_LN_S_HI) {
+        k += 1.0;
+        rem = dd_add(dd_add(rem, dd{-WG_LN_S_HI, 0.0}), dd{-WG_LN_S_LO, 0.0});
+    }
+    double e = exp(rem.hi);
+    double v = __fma_rn(e, rem.lo, e);  // exp(hi + lo) ~ exp(hi)(1 + lo)
+    int kk = (int)k;
+    if (kk >= WG_PLAIN_MIN_N) {
+        r.mant = sign * v * pow2(90 * kk);
+        r.n = 0;
+        r.plain = true;
+    } else {
+        r.mant = sign * v;
+        r.n = kk;
+        r.plain = false;
+    }
+    return r;
+}
+
+// Value of a scaled double as a plain double (rounded; 0 below the double range).
+__device__ __forceinline__ double scaled_to_double(double mant, int n) {
+    if (n == 0) return mant;
+    return scalbn(mant, 90 * n);
+}
+
+// ---------------------------------------------------------------------------
+// Scaled-mode maintenance after a step (integer pipe only, except the one-time
+// conversion to plain doubles).  (cur, prev) share the exponent n.
+//   |cur| > 2^90  -> both * 2^-90, n += 1
+//   0 < |cur| < 2^-90 -> both * 2^90, n -= 1
+//   n >= WG_PLAIN_MIN_N (value >= 2^-900)  -> plain doubles from now on (Sec. 3.2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scaled_fixup(double &cur, double &prev, int &n, bool &plain) {
+    const int e = biased_exp(cur);
+    if (e > 1023 + 90) {
+        cur = exp_shift(cur, -90);
+        prev = exp_shift(prev, -90);
+        n += 1;
+        if (n >= WG_PLAIN_MIN_N) {
+            const double f = pow2(90 * n);  // 2^(90n) >= 2^-810
+            cur *= f;
+            prev *= f;
+            n = 0;
+            plain = true;
+        }
+    } else if (e < 1023 - 90 && e > 0) {
+        cur = exp_shift(cur, 90);
+        prev = exp_shift(prev, 90);
+        n -= 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// F0_l, G_l = F0_l F1_l, F2_l for orders (mb, ms) at order l (Sec. 4.2.2):
+//   F0 = (l+1)(2l+1) P_{l+mb} P_{l-mb} P_{l+ms} P_{l-ms},  F1 = mb ms / (l(l+1)),
+//   F2 = Q_{l+mb} Q_{l-mb} Q_{l+ms} Q_{l-ms} (l+1)/l
+// so that Eq. lrec reads d^{l+1} = (F0 cos(beta) - G) d^l - F2 d^{l-1}.
+// Requires l >= max(mb, ms); at l = 0 and at l = max(mb, ms) the F2 factor is 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void lrec_coefficients(int l, int mb, int ms, const Tables &T, double &f0,
+                                                  double &g, double &f2) {
+    const double pp = (T.P[l + mb] * T.P[l - mb]) * (T.P[l + ms] * T.P[l - ms]);
+    const double qq = (T.Q[l + mb] * T.Q[l - mb]) * (T.Q[l + ms] * T.Q[l - ms]);
+    f0 = ((double)(l + 1) * (double)(2 * l + 1)) * pp;
+    g = f0 * ((double)mb * (double)ms * T.R1[l]);
+    f2 = T.R2[l] * qq;
+}
+
+// ---------------------------------------------------------------------------
+// status word
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void raise_status(int *status, int bit) {
+    if (status) atomicOr(status, bit);
+}
+
+}  // namespace wg

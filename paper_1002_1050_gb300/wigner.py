@@ -1,0 +1,226 @@
+"""Thin Python binding of the C ABI in include/wigner.h (argument marshalling only).
+
+Every function here checks shapes/dtypes/devices of torch tensors, allocates
+outputs when they are not supplied, and passes raw device pointers and the current
+CUDA stream to the library; all computation runs in the library's sm_103a kernels.
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1002_1050_gb300.build``); if it is missing or cannot be loaded,
+every call raises RuntimeError -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+WG_FP64 = 0
+WG_FP32X = 1
+FORMS = {"fp64": WG_FP64, "fp32x": WG_FP32X}
+WG_LMAX = 32767
+
+_ERR = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "device allocation failed",
+        -4: "bounded device wait timed out", -5: "unsupported device", -6: "not supported by this build"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class WignerError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"wigner error {code} ({_ERR.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libwigner_gb300.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} is missing "
+                                   "(run __graft_entry__.build() or python -m paper_1002_1050_gb300.build)")
+            lib = ctypes.CDLL(path)
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            sig = {
+                "wigner_d_table": [I, I, I, I, P, I, P, P, P],
+                "wigner_d_table_backward": [I, I, I, I, P, P, P, P],
+                "wigner_conv_sum": [I, I, I, I, P, P, P, I, P, P, P],
+                "wigner_conv_sum_backward": [I, I, I, I, P, P, P, P, P, P, P, P, I, P],
+                "wigner_conv_sum_batched": [I, P, P],
+                "wigner_batch_plan_create": [P, I, P, I, P],
+                "wigner_batch_run": [P, I, P],
+                "wigner_batch_plan_destroy": [P],
+                "wigner_device_status": [P],
+                "wigner_error_string": [I],
+                "wigner_last_error_message": [],
+                "wigner_version": [],
+                "wigner_built_arch": [],
+                "wigner_fma_peak": [I, I, I, I, P, P, P],
+            }
+            for name, args in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = I
+            lib.wigner_error_string.restype = ctypes.c_char_p
+            lib.wigner_last_error_message.restype = ctypes.c_char_p
+            lib.wigner_batch_plan_destroy.restype = None
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load().wigner_last_error_message().decode(errors="replace")
+        raise WignerError(rc, msg)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_tensor(x, dtype, name):
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library computes on the GPU only)")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return x
+
+
+def _ptr(x):
+    return ctypes.c_void_p(x.data_ptr()) if x is not None else ctypes.c_void_p(0)
+
+
+def _form(form) -> int:
+    if isinstance(form, str):
+        return FORMS[form]
+    return int(form)
+
+
+def wigner_d_table(beta: torch.Tensor, l_max: int, mb_max: int, ms_max: int, form="fp64",
+                   out: torch.Tensor | None = None, counters: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """d[mb][ms][l][j] = d^l_{mb,ms}(beta_j), float64 (mb_max+1, ms_max+1, l_max+1, n_beta)."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    nb = beta.numel()
+    if out is None:
+        out = torch.empty((mb_max + 1, ms_max + 1, l_max + 1, nb), dtype=torch.float64, device=beta.device)
+    _dev_tensor(out, torch.float64, "out")
+    if tuple(out.shape) != (mb_max + 1, ms_max + 1, l_max + 1, nb):
+        raise ValueError("out has the wrong shape")
+    if counters is not None:
+        _dev_tensor(counters, torch.int64, "counters")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_d_table(l_max, mb_max, ms_max, nb, _ptr(beta), _form(form), _ptr(out),
+                                  _ptr(counters), _stream(stream)))
+    return out
+
+
+def wigner_d_table_backward(beta: torch.Tensor, grad_d: torch.Tensor, l_max: int, mb_max: int, ms_max: int,
+                            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """grad_beta[j] = sum grad_d[mb][ms][l][j] d/dbeta d^l_{mb,ms}(beta_j)."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    grad_d = _dev_tensor(grad_d, torch.float64, "grad_d")
+    nb = beta.numel()
+    if tuple(grad_d.shape) != (mb_max + 1, ms_max + 1, l_max + 1, nb):
+        raise ValueError("grad_d has the wrong shape")
+    if out is None:
+        out = torch.empty(nb, dtype=torch.float64, device=beta.device)
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_d_table_backward(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(grad_d), _ptr(out),
+                                           _stream(stream)))
+    return out
+
+
+def _conv_shapes(beta, a, b):
+    if a.dim() != 2 or b.dim() != 2:
+        raise ValueError("a and b must be 2-D: a[l][m_sky], b[l][m_b]")
+    l_max = a.shape[0] - 1
+    if b.shape[0] != l_max + 1:
+        raise ValueError("a and b must have the same number of l rows")
+    return l_max, b.shape[1] - 1, a.shape[1] - 1, beta.numel()
+
+
+def wigner_conv_sum(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, form="fp64",
+                    out: torch.Tensor | None = None, counters: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """C[mb][ms][j] = sum_l conj(b[l][mb]) a[l][ms] d^l_{mb,ms}(beta_j), complex128."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    a = _dev_tensor(a, torch.complex128, "a")
+    b = _dev_tensor(b, torch.complex128, "b")
+    l_max, mb_max, ms_max, nb = _conv_shapes(beta, a, b)
+    if out is None:
+        out = torch.empty((mb_max + 1, ms_max + 1, nb), dtype=torch.complex128, device=beta.device)
+    _dev_tensor(out, torch.complex128, "out")
+    if tuple(out.shape) != (mb_max + 1, ms_max + 1, nb):
+        raise ValueError("out has the wrong shape")
+    if counters is not None:
+        _dev_tensor(counters, torch.int64, "counters")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_conv_sum(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
+                                   _ptr(out), _ptr(counters), _stream(stream)))
+    return out
+
+
+def wigner_conv_sum_backward(beta, a, b, c_fwd, grad_c, need_a=True, need_b=True, need_beta=True,
+                             stream=None):
+    """(grad_a, grad_b, grad_beta) for a real loss with dL/dC = grad_c (PyTorch convention)."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    a = _dev_tensor(a, torch.complex128, "a")
+    b = _dev_tensor(b, torch.complex128, "b")
+    grad_c = _dev_tensor(grad_c, torch.complex128, "grad_c")
+    l_max, mb_max, ms_max, nb = _conv_shapes(beta, a, b)
+    if c_fwd is not None:
+        _dev_tensor(c_fwd, torch.complex128, "c_fwd")
+    ga = torch.empty_like(a) if need_a else None
+    gb = torch.empty_like(b) if need_b else None
+    gbeta = torch.empty_like(beta) if need_beta else None
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_conv_sum_backward(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _ptr(c_fwd),
+                                            _ptr(grad_c), _ptr(ga), _ptr(gb), _ptr(gbeta), WG_FP64,
+                                            _stream(stream)))
+    return ga, gb, gbeta
+
+
+def wigner_device_status(stream=None) -> int:
+    """Synchronise the stream; return (and clear) the library's device status code."""
+    return int(load().wigner_device_status(_stream(stream)))
+
+
+def check_device_status(stream=None):
+    rc = wigner_device_status(stream)
+    _check(rc)
+
+
+def wigner_fma_peak(pipe: int, blocks: int, threads: int, iters: int, stream=None):
+    """Launch the FMA microbenchmark; returns (sink tensor, FMA lane-operations)."""
+    lib = load()
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    ops = ctypes.c_ulonglong(0)
+    _check(lib.wigner_fma_peak(pipe, blocks, threads, iters, _ptr(sink), ctypes.byref(ops), _stream(stream)))
+    return sink, int(ops.value)
+
+
+def exported_symbols():
+    """Names the binding expects the library to export (for the ABI test)."""
+    return ["wigner_d_table", "wigner_d_table_backward", "wigner_conv_sum", "wigner_conv_sum_backward",
+            "wigner_conv_sum_batched", "wigner_batch_plan_create", "wigner_batch_run",
+            "wigner_batch_plan_destroy", "wigner_device_status", "wigner_error_string",
+            "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak"]

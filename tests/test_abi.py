@@ -1,0 +1,78 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every declared symbol,
+and rejects invalid arguments on the host (no GPU needed for any of this)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1002_1050_gb300 import build as B
+from paper_1002_1050_gb300 import wigner as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "wigner.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(wigner_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return W.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("wigner_d_table", "wigner_d_table_backward", "wigner_conv_sum", "wigner_conv_sum_backward",
+                 "wigner_conv_sum_batched", "wigner_device_status", "wigner_fma_peak"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert set(W.exported_symbols()) == set(_declared_functions())
+
+
+def test_version_and_arch(lib):
+    assert lib.wigner_version() >= 1
+    assert lib.wigner_built_arch() == 1003
+    assert lib.wigner_error_string(0) == b"ok"
+    assert lib.wigner_error_string(-1) == b"invalid argument"
+
+
+P = ctypes.c_void_p
+FAKE = P(0x1000)  # never dereferenced: validation fails before any device access
+
+
+@pytest.mark.parametrize("l_max,mb,ms,nb", [(-1, 0, 0, 1), (4, 5, 0, 1), (4, 0, 5, 1), (4, -1, 0, 1),
+                                           (4, 0, 0, -3), (W.WG_LMAX + 1, 0, 0, 1)])
+def test_bad_orders_rejected(lib, l_max, mb, ms, nb):
+    assert lib.wigner_d_table(l_max, mb, ms, nb, FAKE, 0, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum(l_max, mb, ms, nb, FAKE, FAKE, FAKE, 0, FAKE, None, None) == -1
+
+
+def test_null_and_misaligned_pointers_rejected(lib):
+    assert lib.wigner_conv_sum(8, 2, 8, 4, None, FAKE, FAKE, 0, FAKE, None, None) == -1
+    assert b"beta" in lib.wigner_last_error_message()
+    assert lib.wigner_conv_sum(8, 2, 8, 4, FAKE, P(0x1008), FAKE, 0, FAKE, None, None) == -1
+    assert b"aligned" in lib.wigner_last_error_message()
+    assert lib.wigner_d_table(8, 2, 8, 4, FAKE, 0, None, None, None) == -1
+    assert lib.wigner_d_table(8, 2, 8, 4, FAKE, 7, FAKE, None, None) == -1  # unknown form
+    assert lib.wigner_fma_peak(3, 1, 32, 1, FAKE, None, None) == -1
+
+
+def test_empty_angle_set_is_a_noop(lib):
+    # n_beta = 0: nothing to compute, no device touched
+    assert lib.wigner_d_table(8, 2, 8, 0, None, 0, None, None, None) == 0
+    assert lib.wigner_conv_sum(8, 2, 8, 0, None, FAKE, FAKE, 0, None, None, None) == 0
+
+
+def test_binding_rejects_cpu_tensors():
+    import torch
+    with pytest.raises(ValueError):
+        W.wigner_d_table(torch.zeros(3, dtype=torch.float64), 4, 1, 4)

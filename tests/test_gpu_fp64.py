@@ -1,0 +1,113 @@
+"""GPU parity of the FP64 d-table and fused-sum kernels against the CPU oracle.
+
+Tolerance: 1e-11 absolute, elementwise (FP64 path bar).  Inputs are the seeded
+workloads of paper_1002_1050_gb300.inputs; small cases span several l-tiles,
+several angle chunks and ragged tails; the full 4096/8/4096/2048 sum is checked on
+sampled outputs that the oracle computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1002_1050_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def W():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1002_1050_gb300 import wigner
+    wigner.load()
+    return wigner
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_dtable_l256_full(W):
+    """The 256/4/256/64-angle d-table, every element."""
+    L, MB, MS, beta, _, _ = I.make_config("dtable_l256")
+    d = W.wigner_d_table(_cuda(beta), L, MB, MS).cpu().numpy()
+    W.check_device_status()
+    ref = O.d_table(L, MB, MS, beta)
+    err = np.max(np.abs(d - ref))
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("L,MB,MS,NB", [(0, 0, 0, 1), (1, 1, 1, 3), (2, 2, 2, 5), (37, 5, 37, 71),
+                                        (300, 12, 150, 130)])
+def test_dtable_small_ragged(W, L, MB, MS, NB):
+    beta = np.concatenate([[0.0, math.pi], I.beta_uniform(max(NB - 2, 0), 1e-4, math.pi - 1e-4, 3)])[:NB]
+    d = W.wigner_d_table(_cuda(beta), L, MB, MS).cpu().numpy()
+    W.check_device_status()
+    ref = O.d_table(L, MB, MS, beta)
+    assert np.max(np.abs(d - ref)) <= TOL
+
+
+def test_dtable_counters(W):
+    L, MB, MS, beta, _, _ = I.make_config("dtable_l256")
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    W.wigner_d_table(_cuda(beta), L, MB, MS, counters=cnt)
+    assert int(cnt[0]) == I.n_elements(L, MB, MS, beta.size) == 10_607_680
+
+
+def _complex_beam(L, MB, seed):
+    rng = np.random.default_rng(seed)
+    b = I.beam_blm(L, MB, fwhm=0.05) + 0.05j * rng.standard_normal((L + 1, MB + 1))
+    b[np.arange(MB + 1)[None, :] > np.arange(L + 1)[:, None]] = 0
+    return np.ascontiguousarray(b)
+
+
+@pytest.mark.parametrize("L,MB,MS,NB,grid", [(64, 4, 64, 300, "gl"), (200, 8, 120, 513, "uniform"),
+                                             (129, 16, 129, 31, "gl"), (1, 1, 1, 2, "uniform")])
+def test_conv_small_full(W, L, MB, MS, NB, grid):
+    beta = I.beta_gauss_legendre(NB)[0] if grid == "gl" else I.beta_uniform(NB, 1e-3, math.pi - 1e-3, 11)
+    a = I.sky_alm(L, MS, 5)
+    b = _complex_beam(L, MB, 6)
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b)).cpu().numpy()
+    W.check_device_status()
+    ref = O.conv_sum(L, MB, MS, beta, a, b)
+    assert np.max(np.abs(C - ref)) <= TOL
+
+
+def test_conv_endpoints_and_bad_angle(W):
+    L, MB, MS = 40, 3, 40
+    a = I.sky_alm(L, MS, 1)
+    b = _complex_beam(L, MB, 2)
+    beta = np.array([0.0, math.pi, 0.5, 1.0])
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b)).cpu().numpy()
+    W.check_device_status()
+    assert np.max(np.abs(C - O.conv_sum(L, MB, MS, beta, a, b))) <= TOL
+    # an angle outside [0, pi]: its outputs are NaN and the status word reports it
+    beta_bad = np.array([0.5, -0.1, 4.0, 1.0])
+    C = W.wigner_conv_sum(_cuda(beta_bad), _cuda(a), _cuda(b)).cpu().numpy()
+    assert W.wigner_device_status() == -1
+    assert np.all(np.isnan(C[:, :, 1])) and np.all(np.isnan(C[:, :, 2]))
+    assert np.max(np.abs(C[:, :, [0, 3]] - O.conv_sum(L, MB, MS, beta_bad[[0, 3]], a, b))) <= TOL
+    assert W.wigner_device_status() == 0  # cleared
+
+
+def test_conv_l4096_sampled(W):
+    """Full-size fused FP64 sum (L=4096, m_b<=8, m_sky<=4096, 2048 GL angles), sampled outputs."""
+    L, MB, MS, beta, a, b = I.make_config("conv_fp64_l4096")
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), counters=cnt)
+    W.check_device_status()
+    assert int(cnt[0]) == I.n_elements(L, MB, MS, beta.size)
+    rng = np.random.default_rng(0)
+    n = 400
+    idx = np.stack([rng.integers(0, MB + 1, n), rng.integers(0, MS + 1, n), rng.integers(0, beta.size, n)], 1)
+    # always include the extreme columns and angles
+    idx[:4] = [[0, 0, 0], [MB, MS, beta.size - 1], [0, MS, 0], [MB, 0, beta.size - 1]]
+    got = C.cpu().numpy()[idx[:, 0], idx[:, 1], idx[:, 2]]
+    ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
+    assert np.max(np.abs(got - ref)) <= TOL
+    assert np.all(np.isfinite(C.cpu().numpy()))
