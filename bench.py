@@ -342,6 +342,7 @@ def _profile_traffic():
 
 
 def main(argv=None):
+    global N_BETA
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
@@ -355,7 +356,6 @@ def main(argv=None):
     args = p.parse_args(argv)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    global N_BETA
     N_BETA = args.n_beta
     if args.impl == "reference":
         return run_reference(args)

@@ -1,0 +1,403 @@
+// wg_bwd.cu -- adjoints of the fused l-sum and of the d-table (FP64).
+//
+// Gradients of a real loss L in PyTorch's convention for complex tensors
+// (grad z = dL/dRe z + i dL/dIm z), with C_{mb,ms}(beta) = sum_l conj(b_{l,mb}) a_{l,ms} d^l:
+//   grad_a[l][ms] = sum_mb b[l][mb] S[l][mb][ms],   S[l][mb][ms] = sum_j G[mb][ms][j] d^l_{mb,ms}(beta_j)
+//   grad_b[l][mb] = sum_ms a[l][ms] conj(S[l][mb][ms])
+//   grad_beta[j]  = Re sum_{mb,ms} conj(G) sum_l w_l d/dbeta d^l_{mb,ms}(beta_j)
+// The beta-derivative uses Eq. mrec's relation between neighbouring m' (Sec. 2):
+//   d/dbeta d^l_{m,m'} = ((m' cos b - m)/sin b) d^l_{m,m'} - sqrt((l-m')(l+m'+1)) d^l_{m,m'+1}
+// so  sum_l w_l d/dbeta d^l_{mb,ms} = ((ms cos b - mb)/sin b) C_{mb,ms} - E_{mb,ms},
+//     E_{mb,ms}(beta) = sum_l w_{l,mb,ms} sqrt((l-ms)(l+ms+1)) d^l_{mb,ms+1}(beta):
+// a weighted l-sum over the neighbour chain (mb, ms+1).  The chains are recomputed;
+// no d-table is stored.
+//
+// Kernel layout: as the forward kernel (column group x angle chunk per CTA, CPT chains
+// per thread).  For each column (mb, ms') the CTA runs the chains and
+//   * accumulates, per chain, E for column (mb, ms'-1) from the weights of that column;
+//   * forms S[l] = sum over the CTA's angles of G d^l: each lane sums its CPT chains,
+//     a warp reduce-scatter over blocks of 16 l (shuffles) leaves one warp sum per l,
+//     and the warps' sums are added in shared memory; with one angle chunk the value
+//     is stored, with several it is added atomically into the zeroed workspace.
+// Epilogue kernels then form grad_beta (a sum over columns per angle, fixed order)
+// and grad_a, grad_b (sums over m_b or m_sky per l).
+#include <cuda_runtime.h>
+
+#include "wg_common.cuh"
+
+namespace wg {
+
+constexpr int LB = 16;  // l-block of the warp reduce-scatter
+
+// v[0..15] per lane -> lane t holds sum over the warp of v[t & 15] in v[0]
+__device__ __forceinline__ void warp_reduce_scatter16(double (&v)[LB], int lane) {
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const double send = up ? v[i] : v[i + off];
+            const double keep = up ? v[i + off] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+template <int NT, int CPT, int TL>
+__global__ void __launch_bounds__(NT, 1) conv_bwd_kernel(ConvBwdArgs A, Tables T, int n_chunks, int group,
+                                                      int ms_hi, int want_s, int atomic_s, double *partial) {
+    static_assert(TL % LB == 0, "tile must hold whole l-blocks");
+    constexpr int NW = NT / 32;
+    const int item = blockIdx.x;
+    const int chunk = item % n_chunks;
+    const int grp = item / n_chunks;
+    const int MB1 = A.mb_max + 1;
+    const int MS1 = A.ms_max + 1;
+    const int ncol = MB1 * (ms_hi + 1);
+    const int k_begin = grp * group;
+    const int k_end = min(ncol, k_begin + group);
+    const int L = A.l_max;
+    const int NB = A.n_beta;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool want_e = partial != nullptr;
+
+    __shared__ double2 sFG[TL];        // (F0, G)
+    __shared__ double sF2[TL];
+    __shared__ double2 sWE[TL];        // weights of column (mb, ms'-1) times sqrt((l-ms'+1)(l+ms'))
+    __shared__ double2 sRed[TL / LB][NW][LB];
+
+    int jj[CPT];
+    bool valid[CPT];
+    Angle ang[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        jj[c] = chunk * NT * CPT + c * NT + tid;
+        valid[c] = jj[c] < NB;
+        ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
+        if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
+    }
+
+    for (int k = k_begin; k < k_end; ++k) {
+        const int ms = k / MB1, mb = k - ms * MB1;  // this chain column is (mb, ms)
+        const int l0 = mb > ms ? mb : ms;
+        const bool do_s = want_s && ms <= A.ms_max;
+        const bool do_e = want_e && ms >= 1;
+
+        double cur[CPT], prev[CPT], ere[CPT], eim[CPT], gre[CPT], gim[CPT];
+        int nsc[CPT];
+        bool plain[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const Scaled s = seed_value(mb, ms, ang[c], T);
+            cur[c] = s.mant;
+            nsc[c] = s.n;
+            plain[c] = s.plain;
+            prev[c] = 0.0;
+            ere[c] = 0.0;
+            eim[c] = 0.0;
+            gre[c] = 0.0;
+            gim[c] = 0.0;
+            if (do_s && valid[c]) {
+                const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[((size_t)mb * MS1 + ms) * NB + jj[c]];
+                gre[c] = g.x;
+                gim[c] = g.y;
+            }
+        }
+
+        for (int ts = l0; ts <= L; ts += TL) {
+            __syncthreads();
+            for (int i = tid; i < TL; i += NT) {
+                const int l = ts + i;
+                double f0 = 0.0, g = 0.0, f2 = 0.0, wre = 0.0, wim = 0.0;
+                if (l <= L) {
+                    if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
+                    if (do_e) {
+                        const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * MS1 + (ms - 1)];
+                        const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+                        const double sq = sqrt((double)(l - ms + 1) * (double)(l + ms));
+                        wre = (bv.x * av.x + bv.y * av.y) * sq;
+                        wim = (bv.x * av.y - bv.y * av.x) * sq;
+                    }
+                }
+                sFG[i] = make_double2(f0, g);
+                sF2[i] = f2;
+                sWE[i] = make_double2(wre, wim);
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int blk = 0; blk < TL / LB; ++blk) {
+                const int lb = ts + blk * LB;
+                if (lb > L) break;  // uniform over the CTA
+                double sr[LB], si[LB];
+#pragma unroll
+                for (int i = 0; i < LB; ++i) {
+                    const int l = lb + i;
+                    sr[i] = 0.0;
+                    si[i] = 0.0;
+                    if (l <= L) {  // uniform
+                        const int ti = blk * LB + i;
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) {
+                            const double dv = plain[c] ? cur[c] : 0.0;  // scaled values are < 2^-900
+                            if (do_s) {
+                                sr[i] = fma(gre[c], dv, sr[i]);
+                                si[i] = fma(gim[c], dv, si[i]);
+                            }
+                            if (do_e) {
+                                const double2 we = sWE[ti];
+                                ere[c] = fma(we.x, dv, ere[c]);
+                                eim[c] = fma(we.y, dv, eim[c]);
+                            }
+                        }
+                        if (l < L) {
+                            const double2 fg = sFG[ti];
+                            const double f2 = sF2[ti];
+#pragma unroll
+                            for (int c = 0; c < CPT; ++c) {
+                                const double y = fma(fg.x, ang[c].cb, -fg.y);
+                                const double nx = fma(y, cur[c], -(f2 * prev[c]));
+                                prev[c] = cur[c];
+                                cur[c] = nx;
+                                if (!plain[c]) scaled_fixup(cur[c], prev[c], nsc[c], plain[c]);
+                            }
+                        }
+                    }
+                }
+                if (do_s) {
+                    warp_reduce_scatter16(sr, lane);
+                    warp_reduce_scatter16(si, lane);
+                    if (lane < LB) sRed[blk][warp][lane] = make_double2(sr[0], si[0]);
+                }
+            }
+            __syncthreads();
+            if (do_s) {
+                for (int i = tid; i < TL; i += NT) {
+                    const int l = ts + i;
+                    if (l > L) continue;
+                    double re = 0.0, im = 0.0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        const double2 v = sRed[i / LB][w][i % LB];
+                        re += v.x;
+                        im += v.y;
+                    }
+                    double *dst = A.S + 2 * (((size_t)l * MB1 + mb) * MS1 + ms);
+                    if (atomic_s) {
+                        atomicAdd(dst, re);
+                        atomicAdd(dst + 1, im);
+                    } else {
+                        dst[0] = re;
+                        dst[1] = im;
+                    }
+                }
+            }
+        }
+        // beta term for column (mb, ms-1): Re conj(G) (coef C - E), coef = ((ms-1) cos b - mb)/sin b
+        if (do_e) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                if (!valid[c]) continue;
+                const size_t o = ((size_t)mb * MS1 + (ms - 1)) * NB + jj[c];
+                const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[o];
+                const double2 cf = reinterpret_cast<const double2 *>(A.c_fwd)[o];
+                const double coef = ((double)(ms - 1) * ang[c].cb - (double)mb) / ang[c].sb;
+                const double vr = coef * cf.x - ere[c];
+                const double vi = coef * cf.y - eim[c];
+                partial[o] = g.x * vr + g.y * vi;
+            }
+        }
+    }
+}
+
+// grad_beta[j] = sum over columns of partial[col][j] (fixed order); NaN outside (0, pi)
+__global__ void reduce_columns_kernel(const double *partial, int ncol, int n_beta, const double *beta,
+                                      double *grad_beta, int *status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_beta) return;
+    const double b = beta[j];
+    if (!(b > 0.0 && b < WG_PI_HI)) {
+        grad_beta[j] = __longlong_as_double(0x7ff8000000000000LL);
+        if (status) atomicOr(status, WG_DEVERR_BETA);
+        return;
+    }
+    double acc = 0.0;
+    for (int c = 0; c < ncol; ++c) acc += partial[(size_t)c * n_beta + j];
+    grad_beta[j] = acc;
+}
+
+// grad_a[l][ms] = sum_mb b[l][mb] S[l][mb][ms]
+__global__ void grad_a_kernel(const double *S, const double *b, int l_max, int mb_max, int ms_max, double *grad_a) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int MS1 = ms_max + 1, MB1 = mb_max + 1;
+    if (idx >= (size_t)(l_max + 1) * MS1) return;
+    const int l = (int)(idx / MS1), ms = (int)(idx % MS1);
+    double re = 0.0, im = 0.0;
+    for (int mb = 0; mb < MB1; ++mb) {
+        const double2 bv = reinterpret_cast<const double2 *>(b)[(size_t)l * MB1 + mb];
+        const double2 s = reinterpret_cast<const double2 *>(S)[((size_t)l * MB1 + mb) * MS1 + ms];
+        re += bv.x * s.x - bv.y * s.y;
+        im += bv.x * s.y + bv.y * s.x;
+    }
+    reinterpret_cast<double2 *>(grad_a)[idx] = make_double2(re, im);
+}
+
+// grad_b[l][mb] = sum_ms a[l][ms] conj(S[l][mb][ms]); one CTA per (l, mb)
+template <int NT>
+__global__ void __launch_bounds__(NT) grad_b_kernel(const double *S, const double *a, int l_max, int mb_max,
+                                                    int ms_max, double *grad_b) {
+    const int MS1 = ms_max + 1, MB1 = mb_max + 1;
+    const int l = blockIdx.x / MB1, mb = blockIdx.x % MB1;
+    double re = 0.0, im = 0.0;
+    for (int ms = threadIdx.x; ms < MS1; ms += NT) {
+        const double2 av = reinterpret_cast<const double2 *>(a)[(size_t)l * MS1 + ms];
+        const double2 s = reinterpret_cast<const double2 *>(S)[((size_t)l * MB1 + mb) * MS1 + ms];
+        re += av.x * s.x + av.y * s.y;
+        im += av.y * s.x - av.x * s.y;
+    }
+    __shared__ double rr[NT / 32], ri[NT / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, off);
+        im += __shfl_down_sync(0xffffffffu, im, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rr[threadIdx.x >> 5] = re;
+        ri[threadIdx.x >> 5] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, ti = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            tr += rr[w];
+            ti += ri[w];
+        }
+        reinterpret_cast<double2 *>(grad_b)[(size_t)l * MB1 + mb] = make_double2(tr, ti);
+    }
+}
+
+int launch_conv_bwd(const ConvBwdArgs &a, const Tables &t, void *stream_) {
+    constexpr int NT = 128, CPT = 2, TL = 64;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int MB1 = a.mb_max + 1, MS1 = a.ms_max + 1;
+    const bool want_s = a.grad_a || a.grad_b;
+    const bool want_e = a.grad_beta != nullptr;
+    const size_t s_bytes = (size_t)(a.l_max + 1) * MB1 * MS1 * 16;
+    cudaError_t e;
+    if (want_s) {
+        e = cudaMemsetAsync(a.S, 0, s_bytes, stream);
+        if (e != cudaSuccess) return (int)e;
+    }
+    if (a.n_beta > 0 && (want_s || want_e)) {
+        const int per_chunk = NT * CPT;
+        const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
+        const int ms_hi = want_e ? a.ms_max + 1 : a.ms_max;
+        const int ncol = MB1 * (ms_hi + 1);
+        const int group = 4;
+        const long long items = (long long)n_chunks * ((ncol + group - 1) / group);
+        if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+        conv_bwd_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, stream>>>(a, t, n_chunks, group, ms_hi, want_s ? 1 : 0,
+                                                                          n_chunks > 1 ? 1 : 0, want_e ? a.E : nullptr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return (int)e;
+    }
+    if (want_e) {
+        if (a.n_beta > 0) {
+            reduce_columns_kernel<<<(a.n_beta + 255) / 256, 256, 0, stream>>>(a.E, MB1 * MS1, a.n_beta, a.beta,
+                                                                              a.grad_beta, t.status);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return (int)e;
+        }
+    }
+    if (a.grad_a) {
+        const size_t n = (size_t)(a.l_max + 1) * MS1;
+        grad_a_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(a.S, a.b, a.l_max, a.mb_max, a.ms_max, a.grad_a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return (int)e;
+    }
+    if (a.grad_b) {
+        grad_b_kernel<128><<<(unsigned)((a.l_max + 1) * MB1), 128, 0, stream>>>(a.S, a.a, a.l_max, a.mb_max, a.ms_max,
+                                                                                 a.grad_b);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return (int)e;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// d-table adjoint: grad_beta[j] = sum_{mb,ms,l} Gd[mb][ms][l][j] d/dbeta d^l_{mb,ms}(beta_j).
+// For chain column (mb, ms'):  coef' sum_l Gd[mb][ms'][l][j] d^l  -  sum_l s_l Gd[mb][ms'-1][l][j] d^l,
+// coef' = (ms' cos b - mb)/sin b,  s_l = sqrt((l-ms'+1)(l+ms')); per-(column, angle) partials
+// are then summed over columns in a fixed order.
+// ---------------------------------------------------------------------------
+template <int NT, int TL>
+__global__ void __launch_bounds__(NT) dtable_bwd_kernel(DTableBwdArgs A, Tables T, int ms_hi) {
+    const int MB1 = A.mb_max + 1, MS1 = A.ms_max + 1;
+    const int col = blockIdx.x;  // over MB1 * (ms_hi + 1)
+    const int ms = col / MB1, mb = col - ms * MB1;
+    const int j = blockIdx.y * NT + threadIdx.x;
+    const bool valid = j < A.n_beta;
+    const int L = A.l_max;
+    const int l0 = mb > ms ? mb : ms;
+    const size_t NB = (size_t)A.n_beta;
+    const Angle t = make_angle(valid ? A.beta[j] : 1.0);
+    const Scaled s = seed_value(mb, ms, t, T);
+    double cur = s.mant, prev = 0.0;
+    int n = s.n;
+    bool plain = s.plain;
+    const double *g1 = (ms <= A.ms_max) ? A.grad_d + ((size_t)mb * MS1 + ms) * (size_t)(L + 1) * NB : nullptr;
+    const double *g0 = (ms >= 1) ? A.grad_d + ((size_t)mb * MS1 + (ms - 1)) * (size_t)(L + 1) * NB : nullptr;
+    double acc1 = 0.0, acc0 = 0.0;
+    __shared__ double sF0[TL], sG[TL], sF2[TL], sS[TL];
+    for (int ts = l0; ts <= L; ts += TL) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < TL; i += NT) {
+            const int l = ts + i;
+            double f0 = 0.0, g = 0.0, f2 = 0.0, sq = 0.0;
+            if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
+            if (l <= L && ms >= 1) sq = sqrt((double)(l - ms + 1) * (double)(l + ms));
+            sF0[i] = f0;
+            sG[i] = g;
+            sF2[i] = f2;
+            sS[i] = sq;
+        }
+        __syncthreads();
+        const int nl = min(TL, L + 1 - ts);
+        for (int i = 0; i < nl; ++i) {
+            const int l = ts + i;
+            const double dv = plain ? cur : 0.0;
+            if (valid) {
+                if (g1) acc1 = fma(g1[(size_t)l * NB + j], dv, acc1);
+                if (g0) acc0 = fma(g0[(size_t)l * NB + j], sS[i] * dv, acc0);
+            }
+            if (l < L) {
+                const double y = fma(sF0[i], t.cb, -sG[i]);
+                const double nx = fma(y, cur, -(sF2[i] * prev));
+                prev = cur;
+                cur = nx;
+                if (!plain) scaled_fixup(cur, prev, n, plain);
+            }
+        }
+    }
+    if (valid) {
+        const double coef = ((double)ms * t.cb - (double)mb) / t.sb;
+        A.partial[(size_t)col * NB + j] = coef * acc1 - acc0;
+    }
+}
+
+int launch_dtable_bwd(const DTableBwdArgs &a, const Tables &t, void *stream_) {
+    constexpr int NT = 64, TL = 128;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (a.n_beta == 0) return 0;
+    const int ms_hi = a.ms_max + 1;  // the neighbour column ms_max + 1 (empty when ms_max = l_max)
+    const int ncol = (a.mb_max + 1) * (ms_hi + 1);
+    dim3 grid(ncol, (a.n_beta + NT - 1) / NT);
+    dtable_bwd_kernel<NT, TL><<<grid, NT, 0, stream>>>(a, t, ms_hi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    reduce_columns_kernel<<<(a.n_beta + 255) / 256, 256, 0, stream>>>(a.partial, ncol, a.n_beta, a.beta,
+                                                                      a.grad_beta, t.status);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace wg

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int
                 }
             }
         }
-        double2 *out = reinterpret_cast<double2 *>(A.c_out) + (size_t)k * NB;
+        double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             if (valid[c]) {
