@@ -53,6 +53,8 @@ def _open(path):
     I = ctypes.c_int
     lib.oracle_d_table.argtypes = [I, I, I, I, P, I, P]
     lib.oracle_d_table.restype = I
+    lib.oracle_d_column.argtypes = [I, I, I, I, P, P]
+    lib.oracle_d_column.restype = I
     lib.oracle_d_single.argtypes = [I, I, I, ctypes.c_double]
     lib.oracle_d_single.restype = ctypes.c_double
     lib.oracle_conv_sum.argtypes = [I, I, I, I, P, P, P, P]
@@ -110,6 +112,16 @@ def d_table(l_max: int, mb_max: int, ms_max: int, beta, scaling: bool = True, _l
     rc = lib.oracle_d_table(l_max, mb_max, ms_max, beta.size, _ptr(beta), int(scaling), _ptr(out))
     if rc != 0:
         raise ValueError("oracle_d_table: invalid arguments")
+    return out
+
+
+def d_column(l_max: int, mb: int, ms: int, beta) -> np.ndarray:
+    """d[l][j] = d^l_{mb,ms}(beta_j) for one chain column, l = 0..l_max."""
+    lib = _load()
+    beta = _f64(beta)
+    out = np.empty((l_max + 1, beta.size), dtype=np.float64)
+    if lib.oracle_d_column(l_max, mb, ms, beta.size, _ptr(beta), _ptr(out)) != 0:
+        raise ValueError("oracle_d_column: invalid arguments")
     return out
 
 

@@ -248,6 +248,20 @@ int oracle_d_table(int l_max, int mb_max, int ms_max, int n_beta, const double *
     return 0;
 }
 
+/* One chain column d[l][j] = d^l_{mb,ms}(beta_j), l = 0..l_max (zero below max(mb, ms)). */
+int oracle_d_column(int l_max, int mb, int ms, int n_beta, const double *beta, double *d_out) {
+    if (l_max < 0 || mb < 0 || ms < 0 || mb > l_max || ms > l_max || n_beta < 0) return -1;
+    memset(d_out, 0, sizeof(double) * (size_t)(l_max + 1) * n_beta);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int j = 0; j < n_beta; ++j) {
+        angle_t t = make_angle(beta[j]);
+        chain_spec cs = {l_max, mb, ms, &t, 1, 0};
+        dtab_ctx ctx = {d_out, n_beta, j};
+        run_chain(&cs, dtab_visit, &ctx);
+    }
+    return 0;
+}
+
 /* Single element d^l_{m m'}(beta) for 0 <= m, m' <= l (used by sampled checks). */
 typedef struct { int want_l; double val; } one_ctx;
 
