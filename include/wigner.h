@@ -151,6 +151,31 @@ void wigner_batch_plan_destroy(wg_batch_plan *plan);
 int wigner_conv_sum_batched(int n, const wg_instance *inst, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * wigner_conv_sum_noalloc -- wigner_conv_sum (form WG_FP64, no counters) that never
+ * allocates memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot let a library call cudaMalloc -- code running while a CUDA graph is being
+ * captured, applications that hand all device memory to their own pool allocator, and
+ * real-time loops that must not enter the driver's allocator.  wigner_conv_sum keeps
+ * its constant tables in device memory it allocates on first use; this variant runs the
+ * same kernel with those tables in a fixed array of WG_NOALLOC_LMAX-sized tables
+ * (about 640 KiB) compiled into the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   Arguments, layouts and results as wigner_conv_sum.  l_max > WG_NOALLOC_LMAX is
+ *   rejected with WG_ERR_ARG (use wigner_conv_sum for larger problems).
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and fills it with a synchronous
+ *   host-to-device copy (no allocation).  Make that first call before any stream
+ *   capture, and do not overlap it with another call of this entry point on the same
+ *   device: until it returns, the array is being written.  Later calls only read the
+ *   array (its contents never change after set-up), so they may overlap one another.
+ *   It keeps no status word: an angle outside [0, pi] shows only as NaN outputs.
+ *   Calls no cudaMalloc, cudaFree or other allocating routine, on the host heap either.
+ * ------------------------------------------------------------------------- */
+#define WG_NOALLOC_LMAX 8192
+int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                            const wg_c64 *a, const wg_c64 *b, wg_c64 *c_out, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Status and diagnostics
  * ------------------------------------------------------------------------- */
 /* Synchronises `stream`, returns and clears the device status word of the current

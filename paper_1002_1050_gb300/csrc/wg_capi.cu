@@ -188,6 +188,10 @@ int launch_rc(int err, const char *what) {
 
 }  // namespace
 
+namespace wg {
+void set_last_error(const std::string &msg) { g_msg = msg; }
+}  // namespace wg
+
 extern "C" {
 
 int wigner_version(void) { return 1; }

@@ -65,6 +65,7 @@ def load():
                 "wigner_version": [],
                 "wigner_built_arch": [],
                 "wigner_fma_peak": [I, I, I, I, P, P, P],
+                "wigner_conv_sum_noalloc": [I, I, I, I, P, P, P, P, P],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -199,6 +200,24 @@ def wigner_conv_sum_backward(beta, a, b, c_fwd, grad_c, need_a=True, need_b=True
     return ga, gb, gbeta
 
 
+def wigner_conv_sum_noalloc(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor,
+                            stream=None) -> torch.Tensor:
+    """wigner_conv_sum (FP64) through the allocation-free entry point; `out` must be supplied
+    (complex128, (mb_max+1, ms_max+1, n_beta)) and l_max <= 8192."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    a = _dev_tensor(a, torch.complex128, "a")
+    b = _dev_tensor(b, torch.complex128, "b")
+    out = _dev_tensor(out, torch.complex128, "out")
+    l_max, mb_max, ms_max, nb = _conv_shapes(beta, a, b)
+    if tuple(out.shape) != (mb_max + 1, ms_max + 1, nb):
+        raise ValueError("out has the wrong shape")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_conv_sum_noalloc(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _ptr(out),
+                                           _stream(stream)))
+    return out
+
+
 def wigner_device_status(stream=None) -> int:
     """Synchronise the stream; return (and clear) the library's device status code."""
     return int(load().wigner_device_status(_stream(stream)))
@@ -223,4 +242,5 @@ def exported_symbols():
     return ["wigner_d_table", "wigner_d_table_backward", "wigner_conv_sum", "wigner_conv_sum_backward",
             "wigner_conv_sum_batched", "wigner_batch_plan_create", "wigner_batch_run",
             "wigner_batch_plan_destroy", "wigner_device_status", "wigner_error_string",
-            "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak"]
+            "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
+            "wigner_conv_sum_noalloc"]
