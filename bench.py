@@ -281,6 +281,10 @@ def run_ours(args):
     except Exception:
         pass
 
+    fp32x = None
+    if not args.skip_fp32x:
+        fp32x = _fp32x_block(W, dev, stream, args)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -323,11 +327,66 @@ def run_ours(args):
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                      "fma_microbench_tflops": peak_meas},
         "cpu_baseline": cpu,
+        "fp32x": fp32x,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# FP32 FMA peak of the GB300 SM: 128 FP32 lanes/clock/SM
+FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def _fp32x_block(W, dev, stream, args):
+    """The FP32 form on the 8192/16/8192/8192-angle workload: throughput, error against the
+    FP64 kernel (every 16th angle), and speed-up over the FP64 kernel on that same subset."""
+    import torch
+    from paper_1002_1050_gb300 import inputs as I
+
+    L, MB, MS, beta_h, a_h, b_h = I.make_config("conv_fp32x_l8192", n_beta=args.fp32x_n_beta)
+    beta = torch.from_numpy(beta_h).to(dev)
+    a = torch.from_numpy(a_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    out = torch.empty((MB + 1, MS + 1, beta.numel()), dtype=torch.complex128, device=dev)
+    cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+    W.wigner_conv_sum(beta, a, b, form="fp32x", out=out, counters=cnt)
+    W.check_device_status()
+    n_elem, n_sum = int(cnt[0]), int(cnt[1])
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_full = timed(lambda: W.wigner_conv_sum(beta, a, b, form="fp32x", out=out), args.fp32x_steps)
+    sel = torch.arange(0, beta.numel(), 16, device=dev)
+    beta_s = beta[sel].contiguous()
+    out64 = torch.empty((MB + 1, MS + 1, beta_s.numel()), dtype=torch.complex128, device=dev)
+    out32 = torch.empty_like(out64)
+    ms64 = timed(lambda: W.wigner_conv_sum(beta_s, a, b, form="fp64", out=out64), 1)
+    ms32 = timed(lambda: W.wigner_conv_sum(beta_s, a, b, form="fp32x", out=out32), 3)
+    rel = float((torch.linalg.vector_norm(out[:, :, sel] - out64) / torch.linalg.vector_norm(out64)).item())
+    W.check_device_status()
+    flops = 5 * n_elem + 4 * n_sum
+    achieved = flops / (ms_full / 1e3) / 1e12
+    del out, out64, out32
+    torch.cuda.empty_cache()
+    return {"workload": f"conv_fp32x_l8192 (L=8192, m_b<=16, m_sky<=8192, {beta.numel()} Gauss-Legendre angles)",
+            "value": n_elem / (ms_full / 1e3), "unit": "evals/s", "ms_per_launch": ms_full,
+            "dtype": "f32 recursion + int32 exponent carry, f64 seeds/tables, compensated f32 sums",
+            "rel_l2_vs_fp64_kernel": rel, "error_subset": "every 16th angle (512 of 8192)",
+            "speedup_vs_fp64_kernel": ms64 / ms32, "speedup_subset_ms": {"fp64": ms64, "fp32x": ms32},
+            "roofline": {"bound": "alu", "pipe": "fp32_fma", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"}}
 
 
 def _profile_traffic():
@@ -351,6 +410,10 @@ def main(argv=None):
     p.add_argument("--cpu-sample", type=int, default=48, help="angles in the oracle's CPU-baseline sample")
     p.add_argument("--ref-sample", type=int, default=8, help="angles per step in the reference arm")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--skip-fp32x", action="store_true", help="skip the FP32-form measurement")
+    p.add_argument("--fp32x-steps", type=int, default=3)
+    p.add_argument("--fp32x-n-beta", type=int, default=8192,
+                   help="angles of the FP32-form workload (default 8192; smaller only for profiling)")
     p.add_argument("--n-beta", type=int, default=N_BETA,
                    help="angles per GPU (default 2048; smaller only for profiling captures)")
     args = p.parse_args(argv)

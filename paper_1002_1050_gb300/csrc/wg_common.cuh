@@ -141,25 +141,34 @@ struct Scaled {
     bool plain;
 };
 
-__device__ __forceinline__ Scaled seed_value(int mb, int ms, const Angle &t, const Tables &T) {
+// ln|d^{l0}| of the seed in double-double, its sign, and whether the value is exactly 0.
+__device__ __forceinline__ dd seed_log(int mb, int ms, const Angle &t, const Tables &T, double &sign, bool &zero) {
     const int l0 = mb > ms ? mb : ms;
     const int m = mb > ms ? ms : mb;
     const int p = l0 + m, q = l0 - m;
-    Scaled r;
-    if ((p > 0 && t.c_zero) || (q > 0 && t.s_zero)) {  // a factor is exactly 0 (Sec. 3.2 early stop)
-        r.mant = 0.0;
-        r.n = 0;
-        r.plain = true;
-        return r;
-    }
-    const double sign = (mb > ms && (q & 1)) ? -1.0 : 1.0;
+    zero = (p > 0 && t.c_zero) || (q > 0 && t.s_zero);  // a factor is exactly 0 (Sec. 3.2 early stop)
+    sign = (mb > ms && (q & 1)) ? -1.0 : 1.0;
     dd x = {T.lnf_hi[2 * l0], T.lnf_lo[2 * l0]};
     x = dd_add(x, dd_neg(dd{T.lnf_hi[p], T.lnf_lo[p]}));
     x = dd_add(x, dd_neg(dd{T.lnf_hi[q], T.lnf_lo[q]}));
     x.hi *= 0.5;  // exact
     x.lo *= 0.5;
-    if (p > 0) x = dd_add(x, dd_mul_d(dd{t.lnc, 0.0}, (double)p));
-    if (q > 0) x = dd_add(x, dd_mul_d(dd{t.lns, 0.0}, (double)q));
+    if (p > 0 && !zero) x = dd_add(x, dd_mul_d(dd{t.lnc, 0.0}, (double)p));
+    if (q > 0 && !zero) x = dd_add(x, dd_mul_d(dd{t.lns, 0.0}, (double)q));
+    return x;
+}
+
+__device__ __forceinline__ Scaled seed_value(int mb, int ms, const Angle &t, const Tables &T) {
+    Scaled r;
+    double sign;
+    bool zero;
+    dd x = seed_log(mb, ms, t, T, sign, zero);
+    if (zero) {
+        r.mant = 0.0;
+        r.n = 0;
+        r.plain = true;
+        return r;
+    }
     // split x = k * (90 ln 2) + rem, rem in [0, 90 ln 2)
     double k = floor(x.hi * WG_INV_LN_S);
     dd rem = dd_add(x, dd_mul_d(dd{WG_LN_S_HI, 0.0}, -k));  // k * LN_S_HI is exact (|k| < 2^17)

@@ -7,8 +7,6 @@
 
 namespace wg {
 
-int launch_dtable_fp32x(const DTableArgs &, const Tables &, void *) { return (int)cudaErrorNotSupported; }
-int launch_conv_fp32x(const ConvArgs &, const Tables &, void *) { return (int)cudaErrorNotSupported; }
 
 }  // namespace wg
 

@@ -1,0 +1,97 @@
+"""GPU parity of the FP32 form (float recursion with an int32 exponent carry).
+
+Bars: d-table within 2e-4 absolute of the FP64 oracle; C within 1e-4 relative L2 of
+the FP64 kernel and of the FP64 oracle.  The full 8192/16/8192/8192-angle sum is run
+in full; its FP64 comparison uses every 16th angle (the FP64 kernel needs ~40 s for
+all of them) and the oracle checks sampled outputs.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1002_1050_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1002_1050_gb300 import wigner
+    wigner.load()
+    return wigner
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _rel_l2(x, ref):
+    return float(np.linalg.norm((x - ref).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+def test_dtable_fp32x_l256(W):
+    L, MB, MS, beta, _, _ = I.make_config("dtable_l256")
+    d = W.wigner_d_table(_cuda(beta), L, MB, MS, form="fp32x").cpu().numpy()
+    W.check_device_status()
+    ref = O.d_table(L, MB, MS, beta)
+    err = float(np.max(np.abs(d - ref)))
+    assert err <= 2e-4, err
+
+
+@pytest.mark.parametrize("NB", [7, 300])
+def test_dtable_fp32x_poles_and_turning_points(W, NB):
+    """Angles near both poles and across pi/2; orders whose turning point is inside the range."""
+    L, MB, MS = 1500, 16, 1500
+    beta = np.concatenate([[0.0, 1e-4, 3e-4, math.pi / 2, math.pi - 3e-4, math.pi],
+                           I.beta_uniform(max(NB - 6, 1), 1e-3, math.pi - 1e-3, 2)])[:NB]
+    cols = [(0, 0), (16, 16), (3, 700), (16, 1499), (0, 1500)]
+    d = W.wigner_d_table(_cuda(beta), L, MB, MS, form="fp32x")
+    W.check_device_status()
+    for mb, ms in cols:
+        ref = O.d_column(L, mb, ms, beta)
+        got = d[mb, ms].cpu().numpy()
+        assert float(np.max(np.abs(got - ref))) <= 2e-4, (mb, ms)
+
+
+@pytest.mark.parametrize("L,MB,MS,NB", [(64, 4, 64, 300), (200, 8, 120, 513), (700, 16, 700, 97)])
+def test_conv_fp32x_small(W, L, MB, MS, NB):
+    beta = I.beta_gauss_legendre(NB)[0]
+    a = I.sky_alm(L, MS, 5)
+    rng = np.random.default_rng(6)
+    b = I.beam_blm(L, MB, fwhm=0.05) + 0.05j * rng.standard_normal((L + 1, MB + 1))
+    b[np.arange(MB + 1)[None, :] > np.arange(L + 1)[:, None]] = 0
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form="fp32x").cpu().numpy()
+    W.check_device_status()
+    ref = O.conv_sum(L, MB, MS, beta, a, b)
+    assert _rel_l2(C, ref) <= 1e-4
+    assert np.all(np.isfinite(C))
+
+
+def test_conv_fp32x_l8192(W):
+    """Full 8192/16/8192 sum on 8192 GL angles; vs the FP64 kernel (every 16th angle) and the oracle."""
+    L, MB, MS, beta, a, b = I.make_config("conv_fp32x_l8192")
+    beta_d, a_d, b_d = _cuda(beta), _cuda(a), _cuda(b)
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    C32 = W.wigner_conv_sum(beta_d, a_d, b_d, form="fp32x", counters=cnt)
+    W.check_device_status()
+    assert int(cnt[0]) == I.n_elements(L, MB, MS, beta.size)
+    sel = np.arange(0, beta.size, 16)
+    C64 = W.wigner_conv_sum(_cuda(beta[sel]), a_d, b_d, form="fp64")
+    W.check_device_status()
+    sub = C32[:, :, torch.from_numpy(sel).cuda()]
+    rel = float((torch.linalg.vector_norm(sub - C64) / torch.linalg.vector_norm(C64)).item())
+    assert rel <= 1e-4, rel
+    assert bool(torch.isfinite(torch.view_as_real(C32)).all())
+    rng = np.random.default_rng(0)
+    n = 200
+    idx = np.stack([rng.integers(0, MB + 1, n), rng.integers(0, MS + 1, n), rng.integers(0, beta.size, n)], 1)
+    idx[:4] = [[0, 0, 0], [MB, MS, beta.size - 1], [0, 0, beta.size - 1], [MB, 0, 0]]
+    ti = [torch.from_numpy(idx[:, k]).cuda() for k in range(3)]
+    got = C32[ti[0], ti[1], ti[2]].cpu().numpy()
+    ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
+    assert _rel_l2(got, ref) <= 1e-4
