@@ -127,12 +127,29 @@ int wigner_conv_sum_backward(int l_max, int mb_max, int ms_max, int n_beta, cons
                              double *grad_beta, wg_form form, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Batched uneven instances in one persistent launch (Sec. 4.1's per-beta
- * independence, applied across whole convolutions).  Each instance is one
- * wigner_conv_sum call; all run in a single kernel launch that pulls work items
- * (instance, column group, beta chunk) from a queue ordered longest first.
- * inst: HOST array of n descriptors (device pointers inside).  use_graph != 0
- * captures the launch into a CUDA graph cached on the plan and replays it.
+ * Batched uneven instances in one persistent launch.  The chains of different angles
+ * are independent (Sec. 4.1 distributes angle subsets over tasks for this reason), so
+ * whole fused sums of different l_max, mb_max, n_beta and form can share one launch.
+ * Each instance is one wigner_conv_sum problem (same layouts, device pointers inside);
+ * the plan splits every instance into work items (instance, angle chunk, group of chain
+ * columns) sorted longest first, and a persistent kernel (one CTA per resident slot)
+ * pulls them from an atomic counter; no CTA ever waits for another.
+ *
+ * wigner_batch_plan_create: inst is a HOST array of n descriptors (copied).  The plan
+ *   owns device copies of the descriptors and the work list and allocates them here.
+ *   autotune != 0 times the compiled (threads, chains per thread, l-tile) variants on a
+ *   sample of the plan's own items and keeps the fastest -- this RUNS kernels that write
+ *   the instances' outputs on `stream` and synchronises it; the choice is cached per
+ *   process, and in the JSON file named by the environment variable WIGNER_TUNE_CACHE
+ *   if set (key: GPU name + a hash of the instance shapes and forms).
+ * wigner_batch_run: runs every instance (outputs overwritten).  use_graph != 0 captures
+ *   the run (counter reset + persistent kernel) into a CUDA graph on the first call and
+ *   replays it afterwards; the graph keeps the pointers given at plan creation, so the
+ *   instances' buffers must stay allocated (their contents may change between runs).
+ * wigner_batch_plan_destroy: synchronises the last stream the plan ran on, then frees.
+ * wigner_batch_plan_info: chosen variant, number of work items, persistent grid size.
+ * wigner_conv_sum_batched: create (no autotune) + run + destroy; blocks until done.
+ * Errors: WG_ERR_ARG names the first bad instance; WG_ERR_ALLOC / WG_ERR_CUDA.
  * ------------------------------------------------------------------------- */
 typedef struct {
     int l_max, mb_max, ms_max, n_beta;
@@ -148,6 +165,7 @@ int wigner_batch_plan_create(wg_batch_plan **plan, int n, const wg_instance *ins
                              void *stream);
 int wigner_batch_run(wg_batch_plan *plan, int use_graph, void *stream);
 void wigner_batch_plan_destroy(wg_batch_plan *plan);
+int wigner_batch_plan_info(const wg_batch_plan *plan, int *variant, int *n_items, int *grid);
 int wigner_conv_sum_batched(int n, const wg_instance *inst, void *stream);
 
 /* ---------------------------------------------------------------------------

@@ -190,6 +190,7 @@ int launch_rc(int err, const char *what) {
 
 namespace wg {
 void set_last_error(const std::string &msg) { g_msg = msg; }
+int tables_for(int l_max, Tables *t) { return get_tables(l_max, t); }
 }  // namespace wg
 
 extern "C" {

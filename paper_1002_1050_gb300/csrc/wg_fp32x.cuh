@@ -1,0 +1,287 @@
+// wg_fp32x.cu -- the FP32 form: recursion body in float with an int32 exponent carry.
+//
+// Precision design (see the FP32 accuracy study recorded with the project):
+//  * Seeds (Eqs. ini1-ini2, logstart) in double-double, split into a float mantissa
+//    and an int32 count n of factors 2^64:  value = mant * 2^(64 n).
+//  * The coefficient tables of Sec. 4.2.2 (F0, F0*F1, F2) are built in double and
+//    combined, still in double, into the coefficients of a difference form of
+//    Eq. lrec before rounding to float:
+//        Delta_{l+1} = F2_l Delta_l + (K_l - 2 F0_l x^2) d^l,   d^{l+1} = d^l + Delta_{l+1},
+//    with Delta_l = d^l - d^{l-1}, x^2 = sin^2(beta/2), K_l = F0_l (1 - F1_l) - 1 - F2_l.
+//    Straight float recursion loses all accuracy near the poles (cos beta rounds to
+//    1 and the two roots of the recursion merge); in this form the small quantities
+//    (x^2, K_l) carry their own relative precision.  For beta > pi/2 the same form runs
+//    on e^l = (-1)^l d^l, which obeys Eq. lrec with cos beta -> -cos beta and
+//    F1 -> -F1: x^2 = cos^2(beta/2), K_l = F0_l (1 + F1_l) - 1 - F2_l.
+//  * Scaled mode while the value is below 2^-64: mantissa kept in [2^-64, 2^64] by
+//    joint rescaling of (d, Delta) on the integer pipe; plain floats after that.
+//  * Sum C = sum_l w_l d^l in float: terms go into two per-parity partial sums
+//    (even/odd l, so the (-1)^l of the mirrored chains is applied once per tile), and
+//    each tile's partials are added into a Neumaier-compensated float accumulator.
+//    Terms start with the first plain value (|d| >= 2^-64; the paper's 1e-30 skip
+//    drops terms below the FP32 form's resolution anyway).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wg_common.cuh"
+#include "wg_conv_fp64.cuh"  // flush_counters
+
+namespace wg {
+
+#define WG_LN_S32_HI 0x1.62e42fefa0000p+5     /* 64 ln 2, leading 36 bits */
+#define WG_LN_S32_LO 0x1.cf79abc9e3b3ap-34    /* 64 ln 2 - WG_LN_S32_HI   */
+#define WG_INV_LN_S32 0.022542110013890053
+
+struct Seed32 {
+    float mant;
+    int n;  // value = mant * 2^(64 n); n == 0: plain
+};
+
+// value (a double-double logarithm x and a sign) -> float mantissa and 2^64 count
+__device__ __forceinline__ Seed32 seed32(int mb, int ms, const Angle &t, const Tables &T) {
+    double sign;
+    bool zero;
+    dd x = seed_log(mb, ms, t, T, sign, zero);
+    Seed32 r;
+    if (zero) {
+        r.mant = 0.0f;
+        r.n = 0;
+        return r;
+    }
+    double k = floor(x.hi * WG_INV_LN_S32);
+    dd rem = dd_add(x, dd_mul_d(dd{WG_LN_S32_HI, 0.0}, -k));
+    rem = dd_add(rem, dd{-k * WG_LN_S32_LO, 0.0});
+    if (rem.hi < 0.0) {
+        k -= 1.0;
+        rem = dd_add(dd_add(rem, dd{WG_LN_S32_HI, 0.0}), dd{WG_LN_S32_LO, 0.0});
+    } else if (rem.hi >= WG_LN_S32_HI) {
+        k += 1.0;
+        rem = dd_add(dd_add(rem, dd{-WG_LN_S32_HI, 0.0}), dd{-WG_LN_S32_LO, 0.0});
+    }
+    const double e = exp(rem.hi);
+    double v = sign * __fma_rn(e, rem.lo, e);  // in [1, 2^64)
+    int kk = (int)k;
+    if (kk >= -1) {  // value >= 2^-64: plain
+        v *= (kk == 0) ? 1.0 : 0x1p-64;
+        kk = 0;
+    }
+    r.mant = __double2float_rn(v);
+    r.n = kk;
+    return r;
+}
+
+// exponent-field shift of a normal float (zero stays zero)
+__device__ __forceinline__ float fexp_shift(float x, int k) {
+    int b = __float_as_int(x);
+    b += ((b & 0x7fffffff) != 0) ? (k << 23) : 0;
+    return __int_as_float(b);
+}
+
+// scaled-mode maintenance for the pair (cur, aux) sharing the count n (integer pipe)
+__device__ __forceinline__ void fixup32(float &cur, float &aux, int &n) {
+    const int e = (__float_as_int(cur) >> 23) & 0xff;
+    if (e >= 127 + 64) {
+        cur = fexp_shift(cur, -64);
+        aux = fexp_shift(aux, -64);
+        n += 1;
+        if (n == -1) {  // value >= 2^-64: leave scaled mode
+            cur *= 0x1p-64f;
+            aux *= 0x1p-64f;
+            n = 0;
+        }
+    } else if (e < 127 - 64 && e > 0) {
+        cur = fexp_shift(cur, 64);
+        aux = fexp_shift(aux, 64);
+        n -= 1;
+    }
+}
+
+struct Tile32 {
+    float4 *t;  // (A = -2 F0, F2, K0, K1) per l
+    float2 *w;  // (w_re, w_im) per l
+};
+
+// coefficients of the difference form at order l, rounded to float after the double
+// combination (K0, K1 are small where the form matters and keep their own precision)
+__device__ __forceinline__ float4 diff_coefficients(int l, int L, int mb, int ms, const Tables &T) {
+    if (l >= L) return make_float4(0.f, 0.f, 0.f, 0.f);
+    double f0, g, f2;
+    lrec_coefficients(l, mb, ms, T, f0, g, f2);
+    const double k0 = ((f0 - 1.0) - f2) - g;
+    const double k1 = ((f0 - 1.0) - f2) + g;
+    return make_float4(__double2float_rn(-2.0 * f0), __double2float_rn(f2), __double2float_rn(k0),
+                       __double2float_rn(k1));
+}
+
+// Neumaier-compensated float accumulation: (s, c) += v
+__device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
+    const float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+}
+
+// One l-step of CPT chains that are all plain floats: term l into the partial of
+// parity PAR, then the difference-form step to l+1.
+template <int CPT, int PAR>
+__device__ __forceinline__ void step_plain(const float4 tc, const float2 w, const bool (&high)[CPT],
+                                           const float (&x2)[CPT], float (&cur)[CPT], float (&aux)[CPT],
+                                           float (&pr)[2][CPT], float (&pi)[2][CPT]) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        pr[PAR][c] = fmaf(w.x, cur[c], pr[PAR][c]);
+        pi[PAR][c] = fmaf(w.y, cur[c], pi[PAR][c]);
+        const float coef = fmaf(tc.x, x2[c], high[c] ? tc.w : tc.z);
+        aux[c] = fmaf(tc.y, aux[c], coef * cur[c]);
+        cur[c] = cur[c] + aux[c];
+    }
+}
+
+// The same step when some chains of the warp are still scaled (value < 2^-64): those
+// add no term and keep their mantissa in range.
+template <int CPT, int PAR>
+__device__ __forceinline__ void step_scaled(const float4 tc, const float2 w, const bool (&high)[CPT],
+                                            const float (&x2)[CPT], float (&cur)[CPT], float (&aux)[CPT],
+                                            int (&nsc)[CPT], const bool (&valid)[CPT], float (&pr)[2][CPT],
+                                            float (&pi)[2][CPT], unsigned long long &n_sum) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        const bool pl = nsc[c] == 0;
+        pr[PAR][c] = fmaf(pl ? w.x : 0.f, cur[c], pr[PAR][c]);
+        pi[PAR][c] = fmaf(pl ? w.y : 0.f, cur[c], pi[PAR][c]);
+        n_sum += (pl && valid[c]) ? 1 : 0;
+        const float coef = fmaf(tc.x, x2[c], high[c] ? tc.w : tc.z);
+        aux[c] = fmaf(tc.y, aux[c], coef * cur[c]);
+        cur[c] = cur[c] + aux[c];
+        if (!pl) fixup32(cur[c], aux[c], nsc[c]);
+    }
+}
+
+template <int TL>
+struct SmemFp32 {
+    float4 sT[TL];
+    float2 sW[TL];
+};
+
+// One work item of the FP32 form: chain columns k in [k_begin, k_end) (m_sky-major
+// order) for the angle chunk `chunk` (NT*CPT angles).  Every thread of the CTA calls it.
+template <int NT, int CPT, int TL>
+__device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
+                                                int k_end, SmemFp32<TL> &sm, unsigned long long &n_elem,
+                                                unsigned long long &n_sum) {
+    static_assert(TL % 2 == 0, "tile length must be even (parity of l is tracked per tile)");
+    const int MB1 = A.mb_max + 1;
+    const int L = A.l_max;
+    const int NB = A.n_beta;
+    const int tid = threadIdx.x;
+    float4 *sT = sm.sT;
+    float2 *sW = sm.sW;
+
+    int jj[CPT];
+    bool valid[CPT], high[CPT], bad[CPT];
+    float x2[CPT];
+    Angle ang[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        jj[c] = chunk * NT * CPT + c * NT + tid;
+        valid[c] = jj[c] < NB;
+        const double bj = valid[c] ? A.beta[jj[c]] : 1.0;
+        ang[c] = make_angle(bj);
+        bad[c] = ang[c].bad;
+        if (valid[c] && bad[c]) raise_status(T.status, WG_DEVERR_BETA);
+        high[c] = ang[c].cb < 0.0;  // beta > pi/2: mirrored chain e^l = (-1)^l d^l
+        // x^2 = sin^2(beta/2) = (1 - cos b)/2 (low) or cos^2(beta/2) (high), from the half angle
+        double s, co;
+        sincos(0.5 * (bad[c] ? 1.0 : bj), &s, &co);
+        x2[c] = __double2float_rn(high[c] ? co * co : s * s);
+    }
+
+    for (int k = k_begin; k < k_end; ++k) {
+        const int ms = k / MB1, mb = k - ms * MB1;
+        const int l0 = mb > ms ? mb : ms;
+
+        float cur[CPT], aux[CPT], pr[2][CPT], pi[2][CPT], sr[CPT], cr[CPT], si[CPT], ci[CPT];
+        int nsc[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const Seed32 s = seed32(mb, ms, ang[c], T);
+            // mirrored chains start from e^{l0} = (-1)^{l0} d^{l0}
+            cur[c] = (high[c] && (l0 & 1)) ? -s.mant : s.mant;
+            aux[c] = cur[c];  // Delta_{l0} = d^{l0} - d^{l0-1} = d^{l0}
+            nsc[c] = s.n;
+            sr[c] = cr[c] = si[c] = ci[c] = 0.f;
+        }
+        bool warp_plain = false;
+
+        for (int ts = l0; ts <= L; ts += TL) {
+            __syncthreads();
+            for (int i = tid; i < TL; i += NT) {
+                const int l = ts + i;
+                float2 w = make_float2(0.f, 0.f);
+                if (l <= L) {
+                    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
+                    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+                    w = make_float2(__double2float_rn(bv.x * av.x + bv.y * av.y),
+                                    __double2float_rn(bv.x * av.y - bv.y * av.x));
+                }
+                sT[i] = (l <= L) ? diff_coefficients(l, L, mb, ms, T) : make_float4(0.f, 0.f, 0.f, 0.f);
+                sW[i] = w;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                pr[0][c] = pr[1][c] = pi[0][c] = pi[1][c] = 0.f;
+            }
+            const int nl = min(TL, L + 1 - ts);
+            if (!warp_plain) {
+                bool p = true;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) p = p && (nsc[c] == 0);
+                warp_plain = __all_sync(0xffffffffu, p);
+            }
+            if (warp_plain) {
+                // every chain of the warp is a plain float: no bookkeeping in the loop
+                int i = 0;
+                for (; i + 1 < nl; i += 2) {
+                    step_plain<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, pr, pi);
+                    step_plain<CPT, 1>(sT[i + 1], sW[i + 1], high, x2, cur, aux, pr, pi);
+                }
+                if (i < nl) step_plain<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, pr, pi);
+                int nv = 0;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) nv += valid[c] ? 1 : 0;
+                n_sum += (unsigned long long)nl * nv;
+            } else {
+                int i = 0;
+                for (; i + 1 < nl; i += 2) {
+                    step_scaled<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, nsc, valid, pr, pi, n_sum);
+                    step_scaled<CPT, 1>(sT[i + 1], sW[i + 1], high, x2, cur, aux, nsc, valid, pr, pi, n_sum);
+                }
+                if (i < nl) step_scaled<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, nsc, valid, pr, pi, n_sum);
+            }
+            // partials of this tile into the compensated accumulators; the sign of the
+            // odd-offset partial is (-1) for mirrored chains, and the tile's start parity
+            // (that of l0, as TL is even) is applied at the end
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const float sg = high[c] ? -1.f : 1.f;
+                neumaier_add(sr[c], cr[c], pr[0][c] + sg * pr[1][c]);
+                neumaier_add(si[c], ci[c], pi[0][c] + sg * pi[1][c]);
+            }
+        }
+        double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            if (valid[c]) {
+                const double sg = (high[c] && (l0 & 1)) ? -1.0 : 1.0;
+                const double nan = __longlong_as_double(0x7ff8000000000000LL);
+                const double re = sg * ((double)sr[c] + (double)cr[c]);
+                const double im = sg * ((double)si[c] + (double)ci[c]);
+                out[jj[c]] = bad[c] ? make_double2(nan, nan) : make_double2(re, im);
+                n_elem += (unsigned long long)(L + 1 - l0);
+            }
+        }
+    }
+}
+
+}  // namespace wg

@@ -135,6 +135,33 @@ def make_config(name: str, n_beta: int | None = None, beta_slice: slice | None =
     return c["l_max"], c["mb_max"], c["ms_max"], beta, a, b
 
 
+def batch_instances(n: int = 64, seed: int = 0, l_range=(128, 8192), nb_range=(32, 4096),
+                    m_choices=(0, 2, 4, 8, 16)):
+    """Uneven batch of fused-sum problems (the batched workload).
+
+    Instance i draws, from default_rng(seed + i): l_max ~ U[l_range] (integers),
+    mb_max from m_choices (clipped to l_max), n_beta ~ U[nb_range] (integers) on
+    Gauss-Legendre nodes, and the form (0 = FP64, 1 = FP32) with probability 1/2.
+    ms_max = l_max.  All instances share one seeded sky (seed) truncated to their l_max,
+    and the elliptical beam of the other workloads.  Returns a list of dicts with keys
+    l_max, mb_max, ms_max, n_beta, form, beta (numpy), plus the shared sky `a_full`
+    (complex128 [L+1][L+1] for the largest l_max) under key "a_full" of the first dict.
+    """
+    specs = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        l_max = int(rng.integers(l_range[0], l_range[1] + 1))
+        mb = min(int(rng.choice(m_choices)), l_max)
+        nb = int(rng.integers(nb_range[0], nb_range[1] + 1))
+        form = int(rng.random() < 0.5)
+        specs.append(dict(l_max=l_max, mb_max=mb, ms_max=l_max, n_beta=nb, form=form,
+                          beta=beta_gauss_legendre(nb)[0]))
+    lmax = max(sp["l_max"] for sp in specs) if specs else 0
+    if specs:
+        specs[0]["a_full"] = sky_alm(lmax, lmax, seed)
+    return specs
+
+
 def n_elements(l_max: int, mb_max: int, ms_max: int, n_beta: int) -> int:
     """Number of (beta, m_b, m_sky, l) elements with max(m_b, m_sky) <= l <= l_max."""
     total = 0

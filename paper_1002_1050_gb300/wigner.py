@@ -59,6 +59,7 @@ def load():
                 "wigner_batch_plan_create": [P, I, P, I, P],
                 "wigner_batch_run": [P, I, P],
                 "wigner_batch_plan_destroy": [P],
+                "wigner_batch_plan_info": [P, P, P, P],
                 "wigner_device_status": [P],
                 "wigner_error_string": [I],
                 "wigner_last_error_message": [],
@@ -218,6 +219,76 @@ def wigner_conv_sum_noalloc(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor
     return out
 
 
+class WgInstance(ctypes.Structure):
+    """Mirror of the C ABI's wg_instance."""
+    _fields_ = [("l_max", ctypes.c_int), ("mb_max", ctypes.c_int), ("ms_max", ctypes.c_int),
+                ("n_beta", ctypes.c_int), ("form", ctypes.c_int), ("beta", ctypes.c_void_p),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("c_out", ctypes.c_void_p)]
+
+
+def _instances(problems):
+    """problems: list of (beta, a, b, form, out) with CUDA tensors (out may be None)."""
+    arr = (WgInstance * len(problems))()
+    outs, keep = [], []
+    for i, (beta, a, b, form, out) in enumerate(problems):
+        beta = _dev_tensor(beta, torch.float64, "beta")
+        a = _dev_tensor(a, torch.complex128, "a")
+        b = _dev_tensor(b, torch.complex128, "b")
+        l_max, mb_max, ms_max, nb = _conv_shapes(beta, a, b)
+        if out is None:
+            out = torch.empty((mb_max + 1, ms_max + 1, nb), dtype=torch.complex128, device=beta.device)
+        _dev_tensor(out, torch.complex128, "out")
+        if tuple(out.shape) != (mb_max + 1, ms_max + 1, nb):
+            raise ValueError(f"instance {i}: out has the wrong shape")
+        arr[i] = WgInstance(l_max, mb_max, ms_max, nb, _form(form), beta.data_ptr(), a.data_ptr(), b.data_ptr(),
+                            out.data_ptr())
+        outs.append(out)
+        keep.extend([beta, a, b, out])
+    return arr, outs, keep
+
+
+class BatchPlan:
+    """A batch of uneven fused sums run by one persistent launch (wigner_batch_plan_*).
+
+    The tensors passed in are kept alive by the plan (the device code holds their pointers).
+    """
+
+    def __init__(self, problems, autotune: bool = False, stream=None):
+        lib = load()
+        self._arr, self.outputs, self._keep = _instances(problems)
+        self._plan = ctypes.c_void_p(0)
+        _check(lib.wigner_batch_plan_create(ctypes.byref(self._plan), len(problems), self._arr, int(autotune),
+                                            _stream(stream)))
+
+    def run(self, use_graph: bool = False, stream=None):
+        _check(load().wigner_batch_run(self._plan, int(use_graph), _stream(stream)))
+        return self.outputs
+
+    def info(self):
+        v, n, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().wigner_batch_plan_info(self._plan, ctypes.byref(v), ctypes.byref(n), ctypes.byref(g)))
+        return {"variant": v.value, "n_items": n.value, "grid": g.value}
+
+    def close(self):
+        if self._plan:
+            load().wigner_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wigner_conv_sum_batched(problems, stream=None):
+    """Run (beta, a, b, form, out) problems in one persistent launch; returns the outputs.
+    Blocks until the batch has finished."""
+    arr, outs, _keep = _instances(problems)
+    _check(load().wigner_conv_sum_batched(len(problems), arr, _stream(stream)))
+    return outs
+
+
 def wigner_device_status(stream=None) -> int:
     """Synchronise the stream; return (and clear) the library's device status code."""
     return int(load().wigner_device_status(_stream(stream)))
@@ -243,4 +314,4 @@ def exported_symbols():
             "wigner_conv_sum_batched", "wigner_batch_plan_create", "wigner_batch_run",
             "wigner_batch_plan_destroy", "wigner_device_status", "wigner_error_string",
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
-            "wigner_conv_sum_noalloc"]
+            "wigner_conv_sum_noalloc", "wigner_batch_plan_info"]
