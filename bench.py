@@ -281,6 +281,9 @@ def run_ours(args):
     except Exception:
         pass
 
+    fp64s = None
+    if not args.skip_fp64s:
+        fp64s = _fp64s_block(W, beta, a, b, out, stream, args, elems_rank, mean_ms=total_ms / args.steps)
     fp32x = None
     if not args.skip_fp32x:
         fp32x = _fp32x_block(W, dev, stream, args)
@@ -327,6 +330,7 @@ def run_ours(args):
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                      "fma_microbench_tflops": peak_meas},
         "cpu_baseline": cpu,
+        "fp64s": fp64s,
         "fp32x": fp32x,
     }
     print(json.dumps(line), flush=True)
@@ -337,6 +341,36 @@ def run_ours(args):
 
 # FP32 FMA peak of the GB300 SM: 128 FP32 lanes/clock/SM
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def _fp64s_block(W, beta, a, b, out64, stream, args, elems, mean_ms):
+    """The split-pipe FP64 form on the same inputs: throughput, largest difference from the
+    all-double kernel's C, and the algorithmic rate against the FP64 peak."""
+    import torch
+
+    out = torch.empty_like(out64)
+    cnt = torch.zeros(2, dtype=torch.int64, device=out.device)
+    W.wigner_conv_sum(beta, a, b, form="fp64s", out=out, counters=cnt)
+    W.wigner_conv_sum(beta, a, b, form="fp64", out=out64)
+    torch.cuda.synchronize()
+    W.check_device_status()
+    diff = float((out - out64).abs().max())
+    n_elem, n_sum = int(cnt[0]), int(cnt[1])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.fp64s_steps):
+        W.wigner_conv_sum(beta, a, b, form="fp64s", out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.fp64s_steps
+    achieved = (5 * n_elem + 4 * n_sum) / (ms / 1e3) / 1e12
+    return {"workload": WORKLOAD, "value": elems / (ms / 1e3), "unit": "evals/s", "ms_per_launch": ms,
+            "dtype": "f64 recursion (2 FMA/step) + float-float sum on the FP32 pipe",
+            "max_abs_diff_vs_fp64_kernel": diff, "speedup_vs_fp64_kernel": mean_ms / ms,
+            "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "note": "algorithmic flops over the FP64 peak; the sum runs on the FP32 pipe"}}
 
 
 def _fp32x_block(W, dev, stream, args):
@@ -483,6 +517,8 @@ def main(argv=None):
     p.add_argument("--ref-sample", type=int, default=8, help="angles per step in the reference arm")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--skip-fp32x", action="store_true", help="skip the FP32-form measurement")
+    p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
+    p.add_argument("--fp64s-steps", type=int, default=5)
     p.add_argument("--fp32x-steps", type=int, default=3)
     p.add_argument("--fp32x-n-beta", type=int, default=8192,
                    help="angles of the FP32-form workload (default 8192; smaller only for profiling)")

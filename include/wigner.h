@@ -33,10 +33,15 @@
  *   - Execution is asynchronous and stream-ordered on `stream` (a cudaStream_t;
  *     NULL = legacy default stream).  Calls never throw; they return WG_OK (0) or
  *     a negative WG_ERR_* code after validating their arguments on the host.
- *   - Precision forms: WG_FP64 runs everything in IEEE double.  WG_FP32X runs the
- *     recursion body in float with an int32 exponent carry and compensated float
- *     sums, with double for the seeds and for the steps near the double root of
- *     the recursion (turning point / poles); its error is stated per workload.
+ *   - Precision forms: WG_FP64 runs everything in IEEE double.  WG_FP64S ("split
+ *     pipe") runs the recursion in IEEE double with two FMAs per step (the chain is
+ *     carried normalised by a product of the F2 coefficients) and the weighted sum in
+ *     float-float (~48-bit) arithmetic on the FP32 pipe; its C agrees with WG_FP64 to
+ *     ~1e-13 (fused sums only; the d-table and adjoints treat it as WG_FP64).
+ *     WG_FP32X runs the recursion body in float with an int32 exponent carry (a
+ *     difference form of the recursion that keeps float accuracy at the poles and
+ *     turning points) and compensated float sums, with double for the seeds and the
+ *     coefficient tables; its error is stated per workload.
  */
 #ifndef WIGNER_GB300_H
 #define WIGNER_GB300_H
@@ -54,7 +59,7 @@ typedef struct {
     double re, im;
 } wg_c64;
 
-typedef enum { WG_FP64 = 0, WG_FP32X = 1 } wg_form;
+typedef enum { WG_FP64 = 0, WG_FP32X = 1, WG_FP64S = 2 } wg_form;
 
 enum {
     WG_OK = 0,

@@ -238,7 +238,7 @@ int wigner_d_table(int l_max, int mb_max, int ms_max, int n_beta, const double *
                    double *d_out, wg_counter *counters, void *stream) {
     try {
         WG_TRY(check_orders(l_max, mb_max, ms_max, n_beta));
-        if (form != WG_FP64 && form != WG_FP32X) return fail(WG_ERR_ARG, "unknown form");
+        if (form != WG_FP64 && form != WG_FP32X && form != WG_FP64S) return fail(WG_ERR_ARG, "unknown form");
         if (n_beta == 0) return WG_OK;
         WG_TRY(check_ptr(beta, 8, "beta"));
         WG_TRY(check_ptr(d_out, 8, "d_out"));
@@ -246,7 +246,7 @@ int wigner_d_table(int l_max, int mb_max, int ms_max, int n_beta, const double *
         wg::Tables t;
         WG_TRY(get_tables(l_max, &t));
         wg::DTableArgs a{l_max, mb_max, ms_max, n_beta, beta, d_out, counters};
-        if (form == WG_FP64) return launch_rc(wg::launch_dtable_fp64(a, t, stream), "dtable_fp64 launch");
+        if (form != WG_FP32X) return launch_rc(wg::launch_dtable_fp64(a, t, stream), "dtable_fp64 launch");
         return launch_rc(wg::launch_dtable_fp32x(a, t, stream), "dtable_fp32x launch");
     } catch (const std::bad_alloc &) {
         return fail(WG_ERR_ALLOC, "host allocation failed");
@@ -277,7 +277,7 @@ int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
                     const wg_c64 *b, wg_form form, wg_c64 *c_out, wg_counter *counters, void *stream) {
     try {
         WG_TRY(check_orders(l_max, mb_max, ms_max, n_beta));
-        if (form != WG_FP64 && form != WG_FP32X) return fail(WG_ERR_ARG, "unknown form");
+        if (form != WG_FP64 && form != WG_FP32X && form != WG_FP64S) return fail(WG_ERR_ARG, "unknown form");
         if (n_beta == 0) return WG_OK;
         WG_TRY(check_ptr(beta, 8, "beta"));
         WG_TRY(check_ptr(a, 16, "a"));
@@ -289,6 +289,7 @@ int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
         wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b,
                         (double *)c_out, counters};
         if (form == WG_FP64) return launch_rc(wg::launch_conv_fp64(ca, t, stream), "conv_fp64 launch");
+        if (form == WG_FP64S) return launch_rc(wg::launch_conv_fp64v2(ca, t, stream), "conv_fp64s launch");
         return launch_rc(wg::launch_conv_fp32x(ca, t, stream), "conv_fp32x launch");
     } catch (const std::bad_alloc &) {
         return fail(WG_ERR_ALLOC, "host allocation failed");
@@ -300,7 +301,7 @@ int wigner_conv_sum_backward(int l_max, int mb_max, int ms_max, int n_beta, cons
                              wg_c64 *grad_a, wg_c64 *grad_b, double *grad_beta, wg_form form, void *stream) {
     try {
         WG_TRY(check_orders(l_max, mb_max, ms_max, n_beta));
-        if (form != WG_FP64) return fail(WG_ERR_UNSUPPORTED, "the backward pass is FP64 only");
+        if (form != WG_FP64 && form != WG_FP64S) return fail(WG_ERR_UNSUPPORTED, "the backward pass is FP64 only");
         WG_TRY(check_ptr(a, 16, "a"));
         WG_TRY(check_ptr(b, 16, "b"));
         if (grad_a && !aligned(grad_a, 16)) return fail(WG_ERR_ARG, "grad_a misaligned");

@@ -59,6 +59,48 @@ __device__ __forceinline__ dd dd_mul_d(dd x, double k) {
 }
 
 // ---------------------------------------------------------------------------
+// float-float (value = hi + lo in two floats, ~48 significant bits) on the FP32 pipe,
+// from the same error-free transforms in single precision.  Used to move the weighted
+// l-sum off GB300's narrow FP64 pipe.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+// Split a double into float hi + lo with integer and FP32 operations only (no
+// double<->float conversion, which runs on the FP64 unit): hi = x truncated to 24
+// significant bits, lo = the next 24 bits of the remainder.  Valid for
+// 2^-100 <= |x| < 2^127; other inputs give garbage the caller must mask.
+__device__ __forceinline__ ff split_ff(double x) {
+    const long long b = __double_as_longlong(x);
+    const int hi32 = (int)(b >> 32);
+    const int eu = ((hi32 >> 20) & 0x7ff) - 1023;              // unbiased exponent
+    const unsigned sign = (unsigned)hi32 & 0x80000000u;
+    const unsigned long long mant = (unsigned long long)b & 0xfffffffffffffULL;
+    ff r;
+    r.hi = __uint_as_float(sign | ((unsigned)(eu + 127) << 23) | (unsigned)(mant >> 29));
+    const unsigned rem = (unsigned)(mant & 0x1fffffffULL);      // 29 bits below hi's last bit
+    // rem * 2^(eu - 52) = (rem * 2^-29) * 2^(eu - 23), both factors normal for eu >= -100
+    const float scale = __uint_as_float(sign | ((unsigned)(eu - 23 + 127) << 23));
+    r.lo = __fmul_rn(__fmul_rn(__uint2float_rn(rem), 0x1p-29f), scale);
+    return r;
+}
+
+// acc += w * u in float-float (Dekker product with FMA, Knuth TwoSum, Fast2Sum)
+__device__ __forceinline__ void ff_mac(ff &acc, float wh, float wl, float uh, float ul) {
+    const float p = __fmul_rn(wh, uh);
+    float e = __fmaf_rn(wh, uh, -p);
+    e = __fmaf_rn(wh, ul, e);
+    e = __fmaf_rn(wl, uh, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    const float lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+    acc.hi = __fadd_rn(s, lo);
+    acc.lo = __fsub_rn(lo, __fsub_rn(acc.hi, s));
+}
+
+// ---------------------------------------------------------------------------
 // exponent-field helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int biased_exp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }

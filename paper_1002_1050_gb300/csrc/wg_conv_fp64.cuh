@@ -145,6 +145,180 @@ __device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &
     }
 }
 
+// ===========================================================================
+// Second FP64 variant: two FP64 instructions per element.
+//
+// The chain is carried as u^l = d^l / sigma_l with sigma_{l0} = sigma_{l0+1} = 1 and
+// sigma_{l+1} = F2_l sigma_{l-1}; then Eq. lrec reads
+//     u^{l+1} = (F0'_l cos b - G'_l) u^l - u^{l-1},   F0' = F0 rho_l, G' = G rho_l,
+//     rho_l = sigma_l / sigma_{l+1},
+// so a step is two FP64 FMAs (the d^{l-1} product disappears into the normalisation).
+// The term w_l d^l = (w_l sigma_l) u^l goes to a float-float accumulator on the FP32
+// pipe (u split into two floats by integer operations), so the FP64 pipe -- 2 lanes
+// per clock per SM on GB300 -- runs only the recursion; the float-float products and
+// sums are ~48-bit accurate, far below the FP64 path's 1e-11 bar on C.  sigma_l is a
+// product of the F2 coefficients along each parity of l (between 0.01 and 1 for the
+// orders used), computed per l-tile by one thread and applied to the tile's tables.
+// The threshold |d| >= 1e-30 of Sec. 4.2.1 becomes |u| >= 1e-30 / sigma_l per l.
+// ===========================================================================
+template <int TL>
+struct SmemFp64v2 {
+    double2 sA[TL];        // (F0', G')   (phase 1: (F0, G))
+    float4 sW[TL];         // (w' re hi, lo, w' im hi, lo),  w' = conj(b) a sigma_l
+    long long sT[TL];      // bit pattern of 1e-30 / sigma_l
+    double sF2[TL];        // F2_l (phase 1)
+    double2 sWd[TL];       // w_l (phase 1)
+    double sSig[TL + 1];   // sigma_{ts + i}
+};
+
+__device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+}
+
+template <int NT, int CPT, int TL>
+__device__ __forceinline__ void conv_fp64v2_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
+                                                 int k_end, SmemFp64v2<TL> &sm, unsigned long long &n_elem,
+                                                 unsigned long long &n_sum) {
+    const int MB1 = A.mb_max + 1;
+    const int L = A.l_max;
+    const int NB = A.n_beta;
+    const int tid = threadIdx.x;
+
+    int jj[CPT];
+    bool valid[CPT];
+    Angle ang[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        jj[c] = chunk * NT * CPT + c * NT + tid;
+        valid[c] = jj[c] < NB;
+        ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
+        if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
+    }
+
+    for (int k = k_begin; k < k_end; ++k) {
+        const int ms = k / MB1, mb = k - ms * MB1;
+        const int l0 = mb > ms ? mb : ms;
+
+        double u[CPT], up[CPT];
+        ff are[CPT], aim[CPT];
+        int nsc[CPT];
+        bool plain[CPT], summing[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const Scaled s = seed_value(mb, ms, ang[c], T);
+            u[c] = s.mant;  // sigma_{l0} = 1
+            nsc[c] = s.n;
+            plain[c] = s.plain;
+            up[c] = 0.0;
+            are[c] = ff{0.f, 0.f};
+            aim[c] = ff{0.f, 0.f};
+            summing[c] = false;
+        }
+        bool warp_sum = false;
+        double sig_m1 = 0.0, sig_0 = 1.0;  // thread 0's carry: sigma_{ts-1}, sigma_{ts}
+
+        for (int ts = l0; ts <= L; ts += TL) {
+            __syncthreads();
+            for (int i = tid; i < TL; i += NT) {  // phase 1: F0, G, F2, w
+                const int l = ts + i;
+                double f0 = 0.0, g = 0.0, f2 = 0.0;
+                double2 w = make_double2(0.0, 0.0);
+                if (l <= L) {
+                    if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
+                    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
+                    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+                    w = make_double2(bv.x * av.x + bv.y * av.y, bv.x * av.y - bv.y * av.x);
+                }
+                sm.sA[i] = make_double2(f0, g);
+                sm.sF2[i] = f2;
+                sm.sWd[i] = w;
+            }
+            __syncthreads();
+            if (tid == 0) {  // phase 2: sigma_{ts+i}, i = 0..TL
+                double sm1 = sig_m1, s0 = sig_0;
+                sm.sSig[0] = s0;
+                for (int i = 0; i < TL; ++i) {
+                    const int l = ts + i;
+                    double nx;
+                    if (l == l0 || l >= L)
+                        nx = s0;  // sigma_{l0+1} = 1; past l_max: unused, kept finite
+                    else
+                        nx = sm.sF2[i] * sm1;
+                    sm.sSig[i + 1] = nx;
+                    sm1 = s0;
+                    s0 = nx;
+                }
+                sig_m1 = sm1;
+                sig_0 = s0;
+            }
+            __syncthreads();
+            for (int i = tid; i < TL; i += NT) {  // phase 3: normalised tables
+                const int l = ts + i;
+                const double sg = sm.sSig[i];
+                double2 fg = sm.sA[i];
+                if (l < L) {
+                    const double rho = sg / sm.sSig[i + 1];
+                    fg.x *= rho;
+                    fg.y *= rho;
+                }
+                const double2 w = sm.sWd[i];
+                float4 wf;
+                dbl_to_ff(w.x * sg, wf.x, wf.y);
+                dbl_to_ff(w.y * sg, wf.z, wf.w);
+                sm.sA[i] = fg;
+                sm.sW[i] = wf;
+                sm.sT[i] = __double_as_longlong(WG_EPS_SUM / sg);
+            }
+            __syncthreads();
+            const int nl = min(TL, L + 1 - ts);
+            for (int i = 0; i < nl; ++i) {
+                const double2 fg = sm.sA[i];
+                const float4 w = sm.sW[i];
+                const long long thr = sm.sT[i];
+                bool any = false;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    summing[c] = summing[c] || (plain[c] && abs_ge(u[c], thr));
+                    any |= summing[c];
+                }
+                if (!warp_sum) warp_sum = __any_sync(0xffffffffu, any);
+                if (warp_sum) {
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) {
+                        ff uu = split_ff(u[c]);
+                        if (!summing[c]) uu = ff{0.f, 0.f};
+                        ff_mac(are[c], w.x, w.y, uu.hi, uu.lo);
+                        ff_mac(aim[c], w.z, w.w, uu.hi, uu.lo);
+                        n_sum += (summing[c] && valid[c]) ? 1 : 0;
+                    }
+                }
+                if (ts + i < L) {
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) {
+                        const double y = fma(fg.x, ang[c].cb, -fg.y);
+                        const double nx = fma(y, u[c], -up[c]);
+                        up[c] = u[c];
+                        u[c] = nx;
+                        if (!plain[c]) scaled_fixup(u[c], up[c], nsc[c], plain[c]);
+                    }
+                }
+            }
+        }
+        double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            if (valid[c]) {
+                const double nan = __longlong_as_double(0x7ff8000000000000LL);
+                const double re = (double)are[c].hi + (double)are[c].lo;
+                const double im = (double)aim[c].hi + (double)aim[c].lo;
+                out[jj[c]] = ang[c].bad ? make_double2(nan, nan) : make_double2(re, im);
+                n_elem += (unsigned long long)(L + 1 - l0);
+            }
+        }
+    }
+}
+
 // warp-aggregated counter update (one atomic per warp)
 __device__ __forceinline__ void flush_counters(unsigned long long *counters, unsigned long long n_elem,
                                                unsigned long long n_sum) {

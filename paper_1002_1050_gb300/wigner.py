@@ -19,7 +19,8 @@ from . import build as _build
 
 WG_FP64 = 0
 WG_FP32X = 1
-FORMS = {"fp64": WG_FP64, "fp32x": WG_FP32X}
+WG_FP64S = 2
+FORMS = {"fp64": WG_FP64, "fp32x": WG_FP32X, "fp64s": WG_FP64S}
 WG_LMAX = 32767
 
 _ERR = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "device allocation failed",

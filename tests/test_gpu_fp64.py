@@ -66,40 +66,47 @@ def _complex_beam(L, MB, seed):
     return np.ascontiguousarray(b)
 
 
+FORMS = ["fp64", "fp64s"]  # all-double kernel; split-pipe kernel (FP64 recursion, float-float sum)
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("L,MB,MS,NB,grid", [(64, 4, 64, 300, "gl"), (200, 8, 120, 513, "uniform"),
-                                             (129, 16, 129, 31, "gl"), (1, 1, 1, 2, "uniform")])
-def test_conv_small_full(W, L, MB, MS, NB, grid):
+                                             (129, 16, 129, 31, "gl"), (1, 1, 1, 2, "uniform"),
+                                             (700, 3, 700, 40, "uniform")])
+def test_conv_small_full(W, L, MB, MS, NB, grid, form):
     beta = I.beta_gauss_legendre(NB)[0] if grid == "gl" else I.beta_uniform(NB, 1e-3, math.pi - 1e-3, 11)
     a = I.sky_alm(L, MS, 5)
     b = _complex_beam(L, MB, 6)
-    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b)).cpu().numpy()
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form=form).cpu().numpy()
     W.check_device_status()
     ref = O.conv_sum(L, MB, MS, beta, a, b)
     assert np.max(np.abs(C - ref)) <= TOL
 
 
-def test_conv_endpoints_and_bad_angle(W):
+@pytest.mark.parametrize("form", FORMS)
+def test_conv_endpoints_and_bad_angle(W, form):
     L, MB, MS = 40, 3, 40
     a = I.sky_alm(L, MS, 1)
     b = _complex_beam(L, MB, 2)
     beta = np.array([0.0, math.pi, 0.5, 1.0])
-    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b)).cpu().numpy()
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form=form).cpu().numpy()
     W.check_device_status()
     assert np.max(np.abs(C - O.conv_sum(L, MB, MS, beta, a, b))) <= TOL
     # an angle outside [0, pi]: its outputs are NaN and the status word reports it
     beta_bad = np.array([0.5, -0.1, 4.0, 1.0])
-    C = W.wigner_conv_sum(_cuda(beta_bad), _cuda(a), _cuda(b)).cpu().numpy()
+    C = W.wigner_conv_sum(_cuda(beta_bad), _cuda(a), _cuda(b), form=form).cpu().numpy()
     assert W.wigner_device_status() == -1
     assert np.all(np.isnan(C[:, :, 1])) and np.all(np.isnan(C[:, :, 2]))
     assert np.max(np.abs(C[:, :, [0, 3]] - O.conv_sum(L, MB, MS, beta_bad[[0, 3]], a, b))) <= TOL
     assert W.wigner_device_status() == 0  # cleared
 
 
-def test_conv_l4096_sampled(W):
+@pytest.mark.parametrize("form", FORMS)
+def test_conv_l4096_sampled(W, form):
     """Full-size fused FP64 sum (L=4096, m_b<=8, m_sky<=4096, 2048 GL angles), sampled outputs."""
     L, MB, MS, beta, a, b = I.make_config("conv_fp64_l4096")
     cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
-    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), counters=cnt)
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form=form, counters=cnt)
     W.check_device_status()
     assert int(cnt[0]) == I.n_elements(L, MB, MS, beta.size)
     rng = np.random.default_rng(0)
