@@ -53,20 +53,38 @@ std::map<int, DevState> g_dev;
 void build_tables(int lcap, std::vector<double> &h) {
     const size_t n2 = 2 * (size_t)lcap + 2;
     const size_t n1 = (size_t)lcap + 1;
-    h.assign(4 * n2 + 2 * n1, 0.0);
+    // doubles: lnf_hi, lnf_lo, P, Q (n2 each), R1, R2 (n1 each); then float2 copies of
+    // ln n!, P, Q (n2 each), R1, R2 (n1 each), one float2 per double slot
+    h.assign(4 * n2 + 2 * n1 + 3 * n2 + 2 * n1, 0.0);
     double *lnf_hi = h.data(), *lnf_lo = lnf_hi + n2, *P = lnf_lo + n2, *Q = P + n2;
     double *R1 = Q + n2, *R2 = R1 + n1;
+    float *F = reinterpret_cast<float *>(R2 + n1);
+    float *lnf_f = F, *P_f = lnf_f + 2 * n2, *Q_f = P_f + 2 * n2, *R1_f = Q_f + 2 * n2, *R2_f = R1_f + 2 * n1;
+    auto put_ff = [](float *dst, long double v) {
+        const float hi = (float)v;
+        dst[0] = hi;
+        dst[1] = (float)(v - (long double)hi);
+    };
     for (size_t i = 0; i < n2; ++i) {
         long double lf = lgammal((long double)i + 1.0L);
         double hi = (double)lf;
         lnf_hi[i] = hi;
         lnf_lo[i] = (double)(lf - (long double)hi);
-        P[i] = (double)sqrtl(1.0L / ((long double)i + 1.0L));
-        Q[i] = (double)sqrtl((long double)i / ((long double)i + 1.0L));
+        const long double p = sqrtl(1.0L / ((long double)i + 1.0L));
+        const long double q = sqrtl((long double)i / ((long double)i + 1.0L));
+        P[i] = (double)p;
+        Q[i] = (double)q;
+        put_ff(lnf_f + 2 * i, lf);
+        put_ff(P_f + 2 * i, p);
+        put_ff(Q_f + 2 * i, q);
     }
     for (size_t l = 1; l < n1; ++l) {
-        R1[l] = (double)(1.0L / ((long double)l * ((long double)l + 1.0L)));
-        R2[l] = (double)(((long double)l + 1.0L) / (long double)l);
+        const long double r1 = 1.0L / ((long double)l * ((long double)l + 1.0L));
+        const long double r2 = ((long double)l + 1.0L) / (long double)l;
+        R1[l] = (double)r1;
+        R2[l] = (double)r2;
+        put_ff(R1_f + 2 * l, r1);
+        put_ff(R2_f + 2 * l, r2);
     }
 }
 
@@ -125,6 +143,12 @@ int get_tables(int l_max, wg::Tables *t, DevState **out_state = nullptr) {
     t->Q = s.tab + 3 * n2;
     t->R1 = s.tab + 4 * n2;
     t->R2 = s.tab + 4 * n2 + n1;
+    const float2 *F = reinterpret_cast<const float2 *>(s.tab + 4 * n2 + 2 * n1);
+    t->lnf_f = F;
+    t->P_f = F + n2;
+    t->Q_f = F + 2 * n2;
+    t->R1_f = F + 3 * n2;
+    t->R2_f = F + 3 * n2 + n1;
     t->lcap = s.lcap;
     t->status = s.status;
     (void)n1;

@@ -86,6 +86,49 @@ __device__ __forceinline__ ff split_ff(double x) {
     return r;
 }
 
+__device__ __forceinline__ ff ff_fast(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float bb = __fsub_rn(s, x.hi);
+    const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    return ff_fast(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return ff_fast(p, e);
+}
+
+__device__ __forceinline__ ff ff_of(float2 v) { return ff{v.x, v.y}; }
+
+// a non-negative integer below 2^31 as float-float (exact)
+__device__ __forceinline__ ff ff_int(long long n) {
+    const float hi = __ll2float_rz(n);
+    return ff{hi, __ll2float_rn(n - (long long)hi)};
+}
+
+// double -> float on the integer pipe, truncating; |x| < 2^-126 flushes to a signed zero,
+// |x| >= 2^128 saturates to infinity.  (Used where float precision of the value suffices.)
+__device__ __forceinline__ float d2f_trunc(double x) {
+    const long long b = __double_as_longlong(x);
+    const int hi = (int)(b >> 32);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    if (e < -126) return __uint_as_float(sign);
+    if (e > 127) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)(e + 127) << 23) |
+                           (unsigned)(((unsigned long long)b & 0xfffffffffffffULL) >> 29));
+}
+
 // acc += w * u in float-float (Dekker product with FMA, Knuth TwoSum, Fast2Sum)
 __device__ __forceinline__ void ff_mac(ff &acc, float wh, float wl, float uh, float ul) {
     const float p = __fmul_rn(wh, uh);
@@ -118,10 +161,12 @@ __device__ __forceinline__ double exp_shift(double x, int k) {
 // 2^k as a double for -1022 <= k <= 1023
 __device__ __forceinline__ double pow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
 
-// |x| >= y for y > 0, compared on the bit patterns (integer pipe)
+// |x| >= y for y > 0, compared on the bit patterns with the sign bit shifted out.
+// (A sign mask here is recognised as fabs and turned into an FP64 instruction, which
+// costs a full slot of GB300's narrow FP64 pipe; the shift keeps it on the integer pipe.)
 __device__ __forceinline__ bool abs_ge(double x, long long ybits) {
-    long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
-    return b >= ybits;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) << 1;
+    return b >= ((unsigned long long)ybits << 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,6 +209,13 @@ struct Tables {
     const double *Q;       // Q_i = sqrt(i/(i+1))
     const double *R1;      // 1/(l(l+1)), l >= 1  (R1[0] = 0)
     const double *R2;      // (l+1)/l,    l >= 1  (R2[0] = 0)
+    // float-float copies (hi, lo) for the FP32 form's set-up on the FP32 pipe; may be
+    // null for paths that do not use them: ln n!, P_i, Q_i (2*lcap+2 each), R1, R2 (lcap+1)
+    const float2 *lnf_f;
+    const float2 *P_f;
+    const float2 *Q_f;
+    const float2 *R1_f;
+    const float2 *R2_f;
     int lcap;
     int *status;           // device status word (WG_DEVERR_* bits)
 };

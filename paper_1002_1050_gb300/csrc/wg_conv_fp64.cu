@@ -48,7 +48,7 @@ static int launch_conv_fp64v2_t(const ConvArgs &a, const Tables &t, void *stream
 }
 
 int launch_conv_fp64v2(const ConvArgs &a, const Tables &t, void *stream) {
-    return launch_conv_fp64v2_t<128, 2, 128>(a, t, stream, 4);
+    return launch_conv_fp64v2_t<256, 2, 128>(a, t, stream, 4);
 }
 
 template <int NT, int CPT, int TL>

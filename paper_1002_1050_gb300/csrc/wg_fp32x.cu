@@ -33,7 +33,7 @@ static int launch_conv_fp32x_t(const ConvArgs &a, const Tables &t, void *stream,
 }
 
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream) {
-    return launch_conv_fp32x_t<128, 4, 64>(a, t, stream, 4);
+    return launch_conv_fp32x_t<128, 4, 64>(a, t, stream, 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -52,12 +52,10 @@ __global__ void __launch_bounds__(NT) dtable_fp32x_kernel(DTableArgs A, Tables T
     if (valid)
         for (int l = 0; l < l0; ++l) out[(size_t)l * NB + j] = 0.0;
     const double beta = valid ? A.beta[j] : 1.0;
-    const Angle t = make_angle(beta);
+    const Angle32 t = make_angle32(beta);
     if (valid && t.bad) raise_status(T.status, WG_DEVERR_BETA);
-    const bool high = t.cb < 0.0;
-    double s, co;
-    sincos(0.5 * (t.bad ? 1.0 : beta), &s, &co);
-    const float x2 = __double2float_rn(high ? co * co : s * s);
+    const bool high = t.high;
+    const float x2 = t.x2;
     const Seed32 sd = seed32(mb, ms, t, T);
     float cur = (high && (l0 & 1)) ? -sd.mant : sd.mant;
     float aux = cur;

@@ -38,35 +38,83 @@ struct Seed32 {
     int n;  // value = mant * 2^(64 n); n == 0: plain
 };
 
-// value (a double-double logarithm x and a sign) -> float mantissa and 2^64 count
-__device__ __forceinline__ Seed32 seed32(int mb, int ms, const Angle &t, const Tables &T) {
-    double sign;
-    bool zero;
-    dd x = seed_log(mb, ms, t, T, sign, zero);
+// 64 ln 2 in three floats: HI has 11 significant bits so k * HI is exact for |k| < 2^13
+#define WG_LN64F_HI 0x1.62cp+5f
+#define WG_LN64F_MID 0x1.217f7ep-6f
+#define WG_LN64F_LO (-0x1.c610cap-31f)
+#define WG_INV_LN64F 0.022542110013890053f
+
+// Per-angle quantities of the FP32 form (Sec. 4.2.2's precomputation), built once per
+// angle per work item: x^2 of the difference form, the mirrored flag, and the
+// half-angle logarithms as float-float for the seeds.
+struct Angle32 {
+    float x2;     // sin^2(beta/2) (beta <= pi/2) or cos^2(beta/2) (mirrored chain)
+    bool high;    // beta > pi/2: the chain runs on e^l = (-1)^l d^l
+    bool bad;     // beta outside [0, pi] or NaN
+    bool c_zero, s_zero;
+    ff lnc, lns;  // ln cos(beta/2), ln sin(beta/2)
+};
+
+__device__ __forceinline__ ff dbl_ff(double x) {
+    const float hi = __double2float_rn(x);
+    return ff{hi, __double2float_rn(x - (double)hi)};
+}
+
+__device__ __forceinline__ Angle32 make_angle32(double beta) {
+    Angle32 t;
+    t.bad = !(beta >= 0.0 && beta <= WG_PI_HI);
+    const double b = t.bad ? 1.0 : beta;
+    double s, c;
+    sincos(0.5 * b, &s, &c);
+    t.high = c < s;
+    t.x2 = __double2float_rn(t.high ? c * c : s * s);
+    t.s_zero = (s == 0.0);
+    t.c_zero = (c <= 0.0);
+    t.lnc = dbl_ff((c >= s) ? 0.5 * log1p(-s * s) : log(c));
+    t.lns = dbl_ff((s >= c) ? 0.5 * log1p(-c * c) : log(s));
+    return t;
+}
+
+// Seed (Eqs. ini1-ini2 in log form, Eq. logstart) in float-float on the FP32 pipe,
+// split into a float mantissa and a count n of factors 2^64: value = mant * 2^(64 n).
+// The logarithm is good to ~2^-48 relative, the exponential to a few float ulps.
+__device__ __forceinline__ Seed32 seed32(int mb, int ms, const Angle32 &t, const Tables &T) {
+    const int l0 = mb > ms ? mb : ms;
+    const int m = mb > ms ? ms : mb;
+    const int p = l0 + m, q = l0 - m;
     Seed32 r;
-    if (zero) {
+    if ((p > 0 && t.c_zero) || (q > 0 && t.s_zero)) {
         r.mant = 0.0f;
         r.n = 0;
         return r;
     }
-    double k = floor(x.hi * WG_INV_LN_S32);
-    dd rem = dd_add(x, dd_mul_d(dd{WG_LN_S32_HI, 0.0}, -k));
-    rem = dd_add(rem, dd{-k * WG_LN_S32_LO, 0.0});
-    if (rem.hi < 0.0) {
-        k -= 1.0;
-        rem = dd_add(dd_add(rem, dd{WG_LN_S32_HI, 0.0}), dd{WG_LN_S32_LO, 0.0});
-    } else if (rem.hi >= WG_LN_S32_HI) {
-        k += 1.0;
-        rem = dd_add(dd_add(rem, dd{-WG_LN_S32_HI, 0.0}), dd{-WG_LN_S32_LO, 0.0});
+    const float sign = (mb > ms && (q & 1)) ? -1.0f : 1.0f;
+    ff x = ff_add(ff_of(T.lnf_f[2 * l0]), ff_neg(ff_of(T.lnf_f[p])));
+    x = ff_add(x, ff_neg(ff_of(T.lnf_f[q])));
+    x.hi *= 0.5f;
+    x.lo *= 0.5f;
+    if (p > 0) x = ff_add(x, ff_mul(t.lnc, ff_int(p)));
+    if (q > 0) x = ff_add(x, ff_mul(t.lns, ff_int(q)));
+    float k = floorf(x.hi * WG_INV_LN64F);
+    ff rem = ff_add(x, ff{-k * WG_LN64F_HI, 0.0f});
+    rem = ff_add(rem, ff_mul(ff{-k, 0.0f}, ff{WG_LN64F_MID, WG_LN64F_LO}));
+    if (rem.hi < 0.0f) {
+        k -= 1.0f;
+        rem = ff_add(rem, ff{WG_LN64F_HI, 0.0f});
+        rem = ff_add(rem, ff{WG_LN64F_MID, WG_LN64F_LO});
+    } else if (rem.hi >= WG_LN64F_HI + WG_LN64F_MID) {
+        k += 1.0f;
+        rem = ff_add(rem, ff{-WG_LN64F_HI, 0.0f});
+        rem = ff_add(rem, ff{-WG_LN64F_MID, -WG_LN64F_LO});
     }
-    const double e = exp(rem.hi);
-    double v = sign * __fma_rn(e, rem.lo, e);  // in [1, 2^64)
+    const float e = expf(rem.hi);
+    float v = sign * __fmaf_rn(e, rem.lo, e);  // in [1, 2^64)
     int kk = (int)k;
     if (kk >= -1) {  // value >= 2^-64: plain
-        v *= (kk == 0) ? 1.0 : 0x1p-64;
+        v *= (kk == 0) ? 1.0f : 0x1p-64f;
         kk = 0;
     }
-    r.mant = __double2float_rn(v);
+    r.mant = v;
     r.n = kk;
     return r;
 }
@@ -102,16 +150,23 @@ struct Tile32 {
     float2 *w;  // (w_re, w_im) per l
 };
 
-// coefficients of the difference form at order l, rounded to float after the double
-// combination (K0, K1 are small where the form matters and keep their own precision)
+// Coefficients of the difference form at order l (A = -2 F0, F2, K0, K1), built in
+// float-float on the FP32 pipe from the float-float tables and rounded to float:
+// K0 = F0 (1 - F1) - 1 - F2 and K1 = F0 (1 + F1) - 1 - F2 are small where the form
+// matters and keep their relative precision because the cancellation happens in ff.
 __device__ __forceinline__ float4 diff_coefficients(int l, int L, int mb, int ms, const Tables &T) {
     if (l >= L) return make_float4(0.f, 0.f, 0.f, 0.f);
-    double f0, g, f2;
-    lrec_coefficients(l, mb, ms, T, f0, g, f2);
-    const double k0 = ((f0 - 1.0) - f2) - g;
-    const double k1 = ((f0 - 1.0) - f2) + g;
-    return make_float4(__double2float_rn(-2.0 * f0), __double2float_rn(f2), __double2float_rn(k0),
-                       __double2float_rn(k1));
+    const ff pp = ff_mul(ff_mul(ff_of(T.P_f[l + mb]), ff_of(T.P_f[l - mb])),
+                         ff_mul(ff_of(T.P_f[l + ms]), ff_of(T.P_f[l - ms])));
+    const ff qq = ff_mul(ff_mul(ff_of(T.Q_f[l + mb]), ff_of(T.Q_f[l - mb])),
+                         ff_mul(ff_of(T.Q_f[l + ms]), ff_of(T.Q_f[l - ms])));
+    const ff f0 = ff_mul(ff_int((long long)(l + 1) * (2 * l + 1)), pp);
+    const ff g = ff_mul(f0, ff_mul(ff_int((long long)mb * ms), ff_of(T.R1_f[l])));
+    const ff f2 = ff_mul(ff_of(T.R2_f[l]), qq);
+    const ff base = ff_add(ff_add(f0, ff{-1.0f, 0.0f}), ff_neg(f2));
+    const ff k0 = ff_add(base, ff_neg(g));
+    const ff k1 = ff_add(base, g);
+    return make_float4(-2.0f * f0.hi, f2.hi, __fadd_rn(k0.hi, k0.lo), __fadd_rn(k1.hi, k1.lo));
 }
 
 // Neumaier-compensated float accumulation: (s, c) += v
@@ -180,20 +235,16 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
     int jj[CPT];
     bool valid[CPT], high[CPT], bad[CPT];
     float x2[CPT];
-    Angle ang[CPT];
+    Angle32 ang[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
         jj[c] = chunk * NT * CPT + c * NT + tid;
         valid[c] = jj[c] < NB;
-        const double bj = valid[c] ? A.beta[jj[c]] : 1.0;
-        ang[c] = make_angle(bj);
+        ang[c] = make_angle32(valid[c] ? A.beta[jj[c]] : 1.0);
         bad[c] = ang[c].bad;
         if (valid[c] && bad[c]) raise_status(T.status, WG_DEVERR_BETA);
-        high[c] = ang[c].cb < 0.0;  // beta > pi/2: mirrored chain e^l = (-1)^l d^l
-        // x^2 = sin^2(beta/2) = (1 - cos b)/2 (low) or cos^2(beta/2) (high), from the half angle
-        double s, co;
-        sincos(0.5 * (bad[c] ? 1.0 : bj), &s, &co);
-        x2[c] = __double2float_rn(high[c] ? co * co : s * s);
+        high[c] = ang[c].high;
+        x2[c] = ang[c].x2;
     }
 
     for (int k = k_begin; k < k_end; ++k) {
@@ -221,8 +272,9 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 if (l <= L) {
                     const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
                     const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
-                    w = make_float2(__double2float_rn(bv.x * av.x + bv.y * av.y),
-                                    __double2float_rn(bv.x * av.y - bv.y * av.x));
+                    const float ar = d2f_trunc(av.x), ai = d2f_trunc(av.y);
+                    const float br = d2f_trunc(bv.x), bi = d2f_trunc(bv.y);
+                    w = make_float2(__fmaf_rn(br, ar, bi * ai), __fmaf_rn(br, ai, -(bi * ar)));
                 }
                 sT[i] = (l <= L) ? diff_coefficients(l, L, mb, ms, T) : make_float4(0.f, 0.f, 0.f, 0.f);
                 sW[i] = w;
