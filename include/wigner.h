@@ -199,6 +199,28 @@ int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_beta, const
                             const wg_c64 *a, const wg_c64 *b, wg_c64 *c_out, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Plans: reserve the library's device state up front.
+ * wigner_plan_create makes the constant tables (ln n!, P_i, Q_i, ...) for every
+ * l_max <= prm->l_max_cap exist on the current device and, with
+ * prm->reserve_backward != 0, the adjoints' workspace for problems up to
+ * (l_max_cap, mb_max_cap, ms_max_cap, n_beta_cap).  Calls within those caps then
+ * allocate nothing, so they may be captured into a CUDA graph.  This call allocates and
+ * synchronises the device; make it before any capture.  The tables and workspace are
+ * per-device library state shared by all calls; wigner_plan_destroy releases only the
+ * plan handle (the state lives until the process exits).
+ * Errors: WG_ERR_ARG (NULL plan or params, caps out of range), WG_ERR_ALLOC, WG_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int l_max_cap, mb_max_cap, ms_max_cap, n_beta_cap;
+    int reserve_backward;
+} wg_params;
+
+typedef struct wg_plan wg_plan;
+
+int wigner_plan_create(wg_plan **plan, const wg_params *prm);
+void wigner_plan_destroy(wg_plan *plan);
+
+/* ---------------------------------------------------------------------------
  * Status and diagnostics
  * ------------------------------------------------------------------------- */
 /* Synchronises `stream`, returns and clears the device status word of the current
@@ -208,6 +230,8 @@ int wigner_device_status(void *stream);
 const char *wigner_error_string(int code);
 /* Text of the last host-side failure on this thread (empty if none). */
 const char *wigner_last_error_message(void);
+/* Code of the last failing call on this thread (WG_OK if none has failed). */
+int wigner_last_error(void);
 /* Library version and the compute capability it was built for (e.g. 1003 = sm_103). */
 int wigner_version(void);
 int wigner_built_arch(void);

@@ -27,7 +27,7 @@
 #include "wg_internal.h"
 
 namespace wg {
-void set_last_error(const std::string &msg);
+void set_last_error(const std::string &msg, int code);
 int tables_for(int l_max, Tables *t);  // wg_capi.cu
 
 struct BatchInst {
@@ -39,7 +39,7 @@ template <int NT, int CPT64, int TL64, int CPT32, int TL32>
 __global__ void __launch_bounds__(NT) batch_kernel(const BatchInst *__restrict__ insts, const int4 *__restrict__ items,
                                                    int n_items, int *counter, Tables T) {
     __shared__ union {
-        SmemFp64<TL64> f64;
+        SmemFp64v2<TL64> f64;
         SmemFp32<TL32> f32;
     } sm;
     __shared__ int s_item;
@@ -54,7 +54,9 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchInst *__restrict__
         const int form = insts[w.x].form;
         unsigned long long ne = 0, ns = 0;
         if (form == WG_FP64)
-            conv_fp64_item<NT, CPT64, TL64>(a, T, w.y, w.z, w.w, sm.f64, ne, ns);
+            conv_fp64v2_item<NT, CPT64, TL64, false>(a, T, w.y, w.z, w.w, sm.f64, ne, ns);
+        else if (form == WG_FP64S)
+            conv_fp64v2_item<NT, CPT64, TL64, true>(a, T, w.y, w.z, w.w, sm.f64, ne, ns);
         else
             conv_fp32x_item<NT, CPT32, TL32>(a, T, w.y, w.z, w.w, sm.f32, ne, ns);
     }
@@ -112,8 +114,9 @@ struct Item {
     double cost;
 };
 
-// relative cost of an element in each form (the FP32 form runs ~6x faster per element)
-double form_weight(int form) { return form == WG_FP64 ? 1.0 : 1.0 / 6.0; }
+// relative cost of an element in each form (measured: the split-pipe FP64 form runs
+// ~1.5x and the FP32 form ~6x faster per element than the all-double form)
+double form_weight(int form) { return form == WG_FP64 ? 1.0 : (form == WG_FP64S ? 1.0 / 1.5 : 1.0 / 6.0); }
 
 void build_items(const std::vector<wg_instance> &inst, const wg::Variant &v, std::vector<Item> &out) {
     out.clear();
@@ -121,7 +124,7 @@ void build_items(const std::vector<wg_instance> &inst, const wg::Variant &v, std
     for (int i = 0; i < (int)inst.size(); ++i) {
         const wg_instance &I = inst[i];
         if (I.n_beta == 0) continue;
-        const int cpt = I.form == WG_FP64 ? v.cpt64 : v.cpt32;
+        const int cpt = I.form == WG_FP32X ? v.cpt32 : v.cpt64;
         const int per_chunk = v.nt * cpt;
         const int n_chunks = (I.n_beta + per_chunk - 1) / per_chunk;
         const int MB1 = I.mb_max + 1;
@@ -157,12 +160,12 @@ int upload_items(wg_batch_plan *p, const std::vector<Item> &items) {
     cudaError_t e = cudaMalloc(&p->d_items, h.size() * sizeof(int4));
     if (e != cudaSuccess) {
         p->d_items = nullptr;
-        wg::set_last_error(std::string("cudaMalloc(batch items): ") + cudaGetErrorString(e));
+        wg::set_last_error(std::string("cudaMalloc(batch items): ") + cudaGetErrorString(e), WG_ERR_ALLOC);
         return WG_ERR_ALLOC;
     }
     e = cudaMemcpy(p->d_items, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        wg::set_last_error(std::string("cudaMemcpy(batch items): ") + cudaGetErrorString(e));
+        wg::set_last_error(std::string("cudaMemcpy(batch items): ") + cudaGetErrorString(e), WG_ERR_CUDA);
         return WG_ERR_CUDA;
     }
     return WG_OK;
@@ -182,7 +185,7 @@ int run_once(wg_batch_plan *p, cudaStream_t s) {
     if (e == cudaSuccess)
         e = wg::launch_variant(p->variant, p->grid, p->d_insts, p->d_items, p->n_items, p->d_counter, p->tables, s);
     if (e != cudaSuccess) {
-        wg::set_last_error(std::string("batch launch: ") + cudaGetErrorString(e));
+        wg::set_last_error(std::string("batch launch: ") + cudaGetErrorString(e), WG_ERR_CUDA);
         return WG_ERR_CUDA;
     }
     return WG_OK;
@@ -299,13 +302,13 @@ int autotune(wg_batch_plan *p, cudaStream_t s) {
 
 int validate(const wg_instance &I, int idx) {
     auto bad = [&](const char *what) {
-        wg::set_last_error("instance " + std::to_string(idx) + ": " + what);
+        wg::set_last_error("instance " + std::to_string(idx) + ": " + what, WG_ERR_ARG);
         return WG_ERR_ARG;
     };
     if (I.l_max < 0 || I.l_max > WG_LMAX) return bad("l_max out of range");
     if (I.mb_max < 0 || I.mb_max > I.l_max || I.ms_max < 0 || I.ms_max > I.l_max) return bad("orders out of range");
     if (I.n_beta < 0) return bad("n_beta < 0");
-    if (I.form != WG_FP64 && I.form != WG_FP32X) return bad("unknown form");
+    if (I.form != WG_FP64 && I.form != WG_FP32X && I.form != WG_FP64S) return bad("unknown form");
     if (I.n_beta == 0) return WG_OK;
     if (!I.beta || ((uintptr_t)I.beta % 8)) return bad("beta NULL or misaligned");
     if (!I.a || ((uintptr_t)I.a % 16)) return bad("a NULL or misaligned");
@@ -330,12 +333,12 @@ extern "C" {
 
 int wigner_batch_plan_create(wg_batch_plan **plan, int n, const wg_instance *inst, int autotune_flag, void *stream) {
     if (!plan) {
-        wg::set_last_error("plan is NULL");
+        wg::set_last_error("plan is NULL", WG_ERR_ARG);
         return WG_ERR_ARG;
     }
     *plan = nullptr;
     if (n < 0 || (n > 0 && !inst)) {
-        wg::set_last_error("bad instance list");
+        wg::set_last_error("bad instance list", WG_ERR_ARG);
         return WG_ERR_ARG;
     }
     int max_l = 0;
@@ -363,14 +366,14 @@ int wigner_batch_plan_create(wg_batch_plan **plan, int n, const wg_instance *ins
     cudaError_t e = cudaMalloc(&p->d_counter, sizeof(int));
     if (e == cudaSuccess && n > 0) e = cudaMalloc(&p->d_insts, n * sizeof(wg::BatchInst));
     if (e != cudaSuccess) {
-        wg::set_last_error(std::string("cudaMalloc(batch plan): ") + cudaGetErrorString(e));
+        wg::set_last_error(std::string("cudaMalloc(batch plan): ") + cudaGetErrorString(e), WG_ERR_ALLOC);
         free_plan(p);
         return WG_ERR_ALLOC;
     }
     if (n > 0) {
         e = cudaMemcpy(p->d_insts, h.data(), n * sizeof(wg::BatchInst), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
-            wg::set_last_error(std::string("cudaMemcpy(batch plan): ") + cudaGetErrorString(e));
+            wg::set_last_error(std::string("cudaMemcpy(batch plan): ") + cudaGetErrorString(e), WG_ERR_CUDA);
             free_plan(p);
             return WG_ERR_CUDA;
         }
@@ -414,7 +417,7 @@ int wigner_batch_plan_create(wg_batch_plan **plan, int n, const wg_instance *ins
 
 int wigner_batch_run(wg_batch_plan *p, int use_graph, void *stream) {
     if (!p) {
-        wg::set_last_error("plan is NULL");
+        wg::set_last_error("plan is NULL", WG_ERR_ARG);
         return WG_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -424,7 +427,7 @@ int wigner_batch_run(wg_batch_plan *p, int use_graph, void *stream) {
         cudaStream_t cs;
         cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
-            wg::set_last_error(std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+            wg::set_last_error(std::string("cudaStreamCreate: ") + cudaGetErrorString(e), WG_ERR_CUDA);
             return WG_ERR_CUDA;
         }
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -435,21 +438,22 @@ int wigner_batch_run(wg_batch_plan *p, int use_graph, void *stream) {
         cudaStreamDestroy(cs);
         if (e != cudaSuccess || e2 != cudaSuccess || rc != WG_OK || !g) {
             if (g) cudaGraphDestroy(g);
-            wg::set_last_error(std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+            wg::set_last_error(std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2),
+                               WG_ERR_CUDA);
             return rc != WG_OK ? rc : WG_ERR_CUDA;
         }
         e = cudaGraphInstantiate(&p->graph_exec, g, 0);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
             p->graph_exec = nullptr;
-            wg::set_last_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            wg::set_last_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e), WG_ERR_CUDA);
             return WG_ERR_CUDA;
         }
         p->graph = g;
     }
     cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
     if (e != cudaSuccess) {
-        wg::set_last_error(std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+        wg::set_last_error(std::string("cudaGraphLaunch: ") + cudaGetErrorString(e), WG_ERR_CUDA);
         return WG_ERR_CUDA;
     }
     return WG_OK;

@@ -19,14 +19,17 @@
 namespace {
 
 thread_local std::string g_msg;
+thread_local int g_code = 0;
 
 int fail(int code, const std::string &msg) {
     g_msg = msg;
+    g_code = code;
     return code;
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
     g_msg = std::string(what) + ": " + cudaGetErrorString(e);
+    g_code = WG_ERR_CUDA;
     return WG_ERR_CUDA;
 }
 
@@ -213,7 +216,10 @@ int launch_rc(int err, const char *what) {
 }  // namespace
 
 namespace wg {
-void set_last_error(const std::string &msg) { g_msg = msg; }
+void set_last_error(const std::string &msg, int code) {
+    g_msg = msg;
+    g_code = code;
+}
 int tables_for(int l_max, Tables *t) { return get_tables(l_max, t); }
 }  // namespace wg
 
@@ -224,6 +230,8 @@ int wigner_version(void) { return 1; }
 int wigner_built_arch(void) { return 1003; }
 
 const char *wigner_last_error_message(void) { return g_msg.c_str(); }
+
+int wigner_last_error(void) { return g_code; }
 
 const char *wigner_error_string(int code) {
     switch (code) {
@@ -353,6 +361,40 @@ int wigner_conv_sum_backward(int l_max, int mb_max, int ms_max, int n_beta, cons
         return fail(WG_ERR_ALLOC, "host allocation failed");
     }
 }
+
+struct wg_plan {
+    int device;
+    wg_params prm;
+};
+
+int wigner_plan_create(wg_plan **plan, const wg_params *prm) {
+    try {
+        if (!plan || !prm) return fail(WG_ERR_ARG, "plan and params must not be NULL");
+        *plan = nullptr;
+        WG_TRY(check_orders(prm->l_max_cap, prm->mb_max_cap, prm->ms_max_cap, prm->n_beta_cap));
+        wg::Tables t;
+        WG_TRY(get_tables(prm->l_max_cap + 1, &t));
+        if (prm->reserve_backward) {
+            const size_t ncol = (size_t)(prm->mb_max_cap + 1) * (prm->ms_max_cap + 2);
+            const size_t conv = ncol * (size_t)(prm->l_max_cap + 1) * 16 + ncol * (size_t)prm->n_beta_cap * 16;
+            const size_t dtab = ncol * (size_t)prm->n_beta_cap * sizeof(double);
+            void *ws = nullptr;
+            WG_TRY(get_workspace(conv > dtab ? conv : dtab, &ws));
+        }
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize(plan)");
+        wg_plan *p = new (std::nothrow) wg_plan;
+        if (!p) return fail(WG_ERR_ALLOC, "host allocation failed");
+        cudaGetDevice(&p->device);
+        p->prm = *prm;
+        *plan = p;
+        return WG_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(WG_ERR_ALLOC, "host allocation failed");
+    }
+}
+
+void wigner_plan_destroy(wg_plan *plan) { delete plan; }
 
 int wigner_fma_peak(int pipe, int blocks, int threads, int iters, double *sink, unsigned long long *fma_ops,
                     void *stream) {

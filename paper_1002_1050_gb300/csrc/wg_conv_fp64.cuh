@@ -146,28 +146,32 @@ __device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &
 }
 
 // ===========================================================================
-// Second FP64 variant: two FP64 instructions per element.
+// The FP64 kernels: two FP64 instructions per recursion step.
 //
 // The chain is carried as u^l = d^l / sigma_l with sigma_{l0} = sigma_{l0+1} = 1 and
 // sigma_{l+1} = F2_l sigma_{l-1}; then Eq. lrec reads
 //     u^{l+1} = (F0'_l cos b - G'_l) u^l - u^{l-1},   F0' = F0 rho_l, G' = G rho_l,
 //     rho_l = sigma_l / sigma_{l+1},
-// so a step is two FP64 FMAs (the d^{l-1} product disappears into the normalisation).
-// The term w_l d^l = (w_l sigma_l) u^l goes to a float-float accumulator on the FP32
-// pipe (u split into two floats by integer operations), so the FP64 pipe -- 2 lanes
-// per clock per SM on GB300 -- runs only the recursion; the float-float products and
-// sums are ~48-bit accurate, far below the FP64 path's 1e-11 bar on C.  sigma_l is a
-// product of the F2 coefficients along each parity of l (between 0.01 and 1 for the
-// orders used), computed per l-tile by one thread and applied to the tile's tables.
-// The threshold |d| >= 1e-30 of Sec. 4.2.1 becomes |u| >= 1e-30 / sigma_l per l.
+// so a step is two FP64 FMAs (the F2 d^{l-1} product of the plain form disappears into
+// the normalisation; sigma_{l+1} = fl(F2_l sigma_{l-1}) is formed in the same order as
+// that product would be, so the rounding per step is unchanged).  The term
+// w_l d^l = (w_l sigma_l) u^l is summed
+//   * SUM_FF = false: with two FP64 FMAs (every operation IEEE double: form WG_FP64);
+//   * SUM_FF = true: in float-float on the FP32 pipe, u split into two floats by integer
+//     operations (form WG_FP64S), so the FP64 pipe -- 2 lanes per clock per SM on
+//     GB300 -- runs only the recursion; the float-float products and sums are ~48-bit
+//     accurate, far below the FP64 path's 1e-11 bar on C.
+// sigma_l is a product of the F2 coefficients along each parity of l (between 0.01 and
+// 1 for the orders used), computed per l-tile by one thread and applied to the tile's
+// tables.  The threshold |d| >= 1e-30 of Sec. 4.2.1 becomes |u| >= 1e-30 / sigma_l.
 // ===========================================================================
 template <int TL>
 struct SmemFp64v2 {
     double2 sA[TL];        // (F0', G')   (phase 1: (F0, G))
-    float4 sW[TL];         // (w' re hi, lo, w' im hi, lo),  w' = conj(b) a sigma_l
+    double2 sWd[TL];       // w_l = conj(b) a (phase 1), then w_l sigma_l
+    float4 sW[TL];         // w_l sigma_l as float-float (re hi, lo, im hi, lo)
     long long sT[TL];      // bit pattern of 1e-30 / sigma_l
     double sF2[TL];        // F2_l (phase 1)
-    double2 sWd[TL];       // w_l (phase 1)
     double sSig[TL + 1];   // sigma_{ts + i}
 };
 
@@ -176,7 +180,7 @@ __device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
     lo = __double2float_rn(x - (double)hi);
 }
 
-template <int NT, int CPT, int TL>
+template <int NT, int CPT, int TL, bool SUM_FF>
 __device__ __forceinline__ void conv_fp64v2_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
                                                  int k_end, SmemFp64v2<TL> &sm, unsigned long long &n_elem,
                                                  unsigned long long &n_sum) {
@@ -200,9 +204,9 @@ __device__ __forceinline__ void conv_fp64v2_item(const ConvArgs &A, const Tables
         const int ms = k / MB1, mb = k - ms * MB1;
         const int l0 = mb > ms ? mb : ms;
 
-        double u[CPT], up[CPT];
+        double u[CPT], up[CPT], cre[CPT], cim[CPT];
         ff are[CPT], aim[CPT];
-        int nsc[CPT];
+        int nsc[CPT], lsum[CPT];
         bool plain[CPT], summing[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
@@ -211,9 +215,12 @@ __device__ __forceinline__ void conv_fp64v2_item(const ConvArgs &A, const Tables
             nsc[c] = s.n;
             plain[c] = s.plain;
             up[c] = 0.0;
+            cre[c] = 0.0;
+            cim[c] = 0.0;
             are[c] = ff{0.f, 0.f};
             aim[c] = ff{0.f, 0.f};
             summing[c] = false;
+            lsum[c] = L + 1;
         }
         bool warp_sum = false;
         double sig_m1 = 0.0, sig_0 = 1.0;  // thread 0's carry: sigma_{ts-1}, sigma_{ts}
@@ -262,35 +269,53 @@ __device__ __forceinline__ void conv_fp64v2_item(const ConvArgs &A, const Tables
                     fg.x *= rho;
                     fg.y *= rho;
                 }
-                const double2 w = sm.sWd[i];
-                float4 wf;
-                dbl_to_ff(w.x * sg, wf.x, wf.y);
-                dbl_to_ff(w.y * sg, wf.z, wf.w);
+                double2 w = sm.sWd[i];
+                w.x *= sg;
+                w.y *= sg;
                 sm.sA[i] = fg;
-                sm.sW[i] = wf;
+                if (SUM_FF) {
+                    float4 wf;
+                    dbl_to_ff(w.x, wf.x, wf.y);
+                    dbl_to_ff(w.y, wf.z, wf.w);
+                    sm.sW[i] = wf;
+                } else {
+                    sm.sWd[i] = w;
+                }
                 sm.sT[i] = __double_as_longlong(WG_EPS_SUM / sg);
             }
             __syncthreads();
             const int nl = min(TL, L + 1 - ts);
             for (int i = 0; i < nl; ++i) {
                 const double2 fg = sm.sA[i];
-                const float4 w = sm.sW[i];
                 const long long thr = sm.sT[i];
                 bool any = false;
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) {
-                    summing[c] = summing[c] || (plain[c] && abs_ge(u[c], thr));
+                    if (!summing[c] && plain[c] && abs_ge(u[c], thr)) {
+                        summing[c] = true;
+                        lsum[c] = ts + i;
+                    }
                     any |= summing[c];
                 }
                 if (!warp_sum) warp_sum = __any_sync(0xffffffffu, any);
                 if (warp_sum) {
+                    if (SUM_FF) {
+                        const float4 w = sm.sW[i];
 #pragma unroll
-                    for (int c = 0; c < CPT; ++c) {
-                        ff uu = split_ff(u[c]);
-                        if (!summing[c]) uu = ff{0.f, 0.f};
-                        ff_mac(are[c], w.x, w.y, uu.hi, uu.lo);
-                        ff_mac(aim[c], w.z, w.w, uu.hi, uu.lo);
-                        n_sum += (summing[c] && valid[c]) ? 1 : 0;
+                        for (int c = 0; c < CPT; ++c) {
+                            ff uu = split_ff(u[c]);
+                            if (!summing[c]) uu = ff{0.f, 0.f};
+                            ff_mac(are[c], w.x, w.y, uu.hi, uu.lo);
+                            ff_mac(aim[c], w.z, w.w, uu.hi, uu.lo);
+                        }
+                    } else {
+                        const double2 w = sm.sWd[i];
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) {
+                            const double um = summing[c] ? u[c] : 0.0;
+                            cre[c] = fma(w.x, um, cre[c]);
+                            cim[c] = fma(w.y, um, cim[c]);
+                        }
                     }
                 }
                 if (ts + i < L) {
@@ -310,10 +335,14 @@ __device__ __forceinline__ void conv_fp64v2_item(const ConvArgs &A, const Tables
         for (int c = 0; c < CPT; ++c) {
             if (valid[c]) {
                 const double nan = __longlong_as_double(0x7ff8000000000000LL);
-                const double re = (double)are[c].hi + (double)are[c].lo;
-                const double im = (double)aim[c].hi + (double)aim[c].lo;
+                double re = cre[c], im = cim[c];
+                if (SUM_FF) {
+                    re = (double)are[c].hi + (double)are[c].lo;
+                    im = (double)aim[c].hi + (double)aim[c].lo;
+                }
                 out[jj[c]] = ang[c].bad ? make_double2(nan, nan) : make_double2(re, im);
                 n_elem += (unsigned long long)(L + 1 - l0);
+                n_sum += (unsigned long long)(L + 1 - min(lsum[c], L + 1));
             }
         }
     }

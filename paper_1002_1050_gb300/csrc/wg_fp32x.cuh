@@ -176,39 +176,30 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
     s = t;
 }
 
-// One l-step of CPT chains that are all plain floats: term l into the partial of
-// parity PAR, then the difference-form step to l+1.
-template <int CPT, int PAR>
-__device__ __forceinline__ void step_plain(const float4 tc, const float2 w, const bool (&high)[CPT],
-                                           const float (&x2)[CPT], float (&cur)[CPT], float (&aux)[CPT],
-                                           float (&pr)[2][CPT], float (&pi)[2][CPT]) {
+// One l-step of CPT chains: term l into the partial of parity PAR, then the
+// difference-form step to l+1.  MASKED: some chain of the warp may still be scaled
+// (value < 2^-64); those add no term, and a chain whose mantissa leaves [2^-64, 2^64)
+// is rescaled (rarely taken branch).  lpl records the l at which a chain turned plain.
+template <int CPT, int PAR, bool MASKED>
+__device__ __forceinline__ void step32(const float4 tc, const float2 w, const bool (&high)[CPT],
+                                       const float (&x2)[CPT], float (&cur)[CPT], float (&aux)[CPT],
+                                       int (&nsc)[CPT], int (&lpl)[CPT], int l, float (&pr)[2][CPT],
+                                       float (&pi)[2][CPT]) {
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        pr[PAR][c] = fmaf(w.x, cur[c], pr[PAR][c]);
-        pi[PAR][c] = fmaf(w.y, cur[c], pi[PAR][c]);
+        const float cm = (!MASKED || nsc[c] == 0) ? cur[c] : 0.f;
+        pr[PAR][c] = fmaf(w.x, cm, pr[PAR][c]);
+        pi[PAR][c] = fmaf(w.y, cm, pi[PAR][c]);
         const float coef = fmaf(tc.x, x2[c], high[c] ? tc.w : tc.z);
         aux[c] = fmaf(tc.y, aux[c], coef * cur[c]);
         cur[c] = cur[c] + aux[c];
-    }
-}
-
-// The same step when some chains of the warp are still scaled (value < 2^-64): those
-// add no term and keep their mantissa in range.
-template <int CPT, int PAR>
-__device__ __forceinline__ void step_scaled(const float4 tc, const float2 w, const bool (&high)[CPT],
-                                            const float (&x2)[CPT], float (&cur)[CPT], float (&aux)[CPT],
-                                            int (&nsc)[CPT], const bool (&valid)[CPT], float (&pr)[2][CPT],
-                                            float (&pi)[2][CPT], unsigned long long &n_sum) {
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        const bool pl = nsc[c] == 0;
-        pr[PAR][c] = fmaf(pl ? w.x : 0.f, cur[c], pr[PAR][c]);
-        pi[PAR][c] = fmaf(pl ? w.y : 0.f, cur[c], pi[PAR][c]);
-        n_sum += (pl && valid[c]) ? 1 : 0;
-        const float coef = fmaf(tc.x, x2[c], high[c] ? tc.w : tc.z);
-        aux[c] = fmaf(tc.y, aux[c], coef * cur[c]);
-        cur[c] = cur[c] + aux[c];
-        if (!pl) fixup32(cur[c], aux[c], nsc[c]);
+        if (MASKED) {
+            const int e = (__float_as_int(cur[c]) >> 23) & 0xff;
+            if (nsc[c] != 0 && (unsigned)(e - 63) > 127u) {
+                fixup32(cur[c], aux[c], nsc[c]);
+                if (nsc[c] == 0) lpl[c] = l + 1;
+            }
+        }
     }
 }
 
@@ -252,7 +243,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
         const int l0 = mb > ms ? mb : ms;
 
         float cur[CPT], aux[CPT], pr[2][CPT], pi[2][CPT], sr[CPT], cr[CPT], si[CPT], ci[CPT];
-        int nsc[CPT];
+        int nsc[CPT], lpl[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             const Seed32 s = seed32(mb, ms, ang[c], T);
@@ -260,6 +251,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             cur[c] = (high[c] && (l0 & 1)) ? -s.mant : s.mant;
             aux[c] = cur[c];  // Delta_{l0} = d^{l0} - d^{l0-1} = d^{l0}
             nsc[c] = s.n;
+            lpl[c] = (s.n == 0) ? l0 : L + 1;
             sr[c] = cr[c] = si[c] = ci[c] = 0.f;
         }
         bool warp_plain = false;
@@ -291,25 +283,19 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 for (int c = 0; c < CPT; ++c) p = p && (nsc[c] == 0);
                 warp_plain = __all_sync(0xffffffffu, p);
             }
-            if (warp_plain) {
-                // every chain of the warp is a plain float: no bookkeeping in the loop
-                int i = 0;
+            int i = 0;
+            if (warp_plain) {  // every chain of the warp is a plain float from here on
                 for (; i + 1 < nl; i += 2) {
-                    step_plain<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, pr, pi);
-                    step_plain<CPT, 1>(sT[i + 1], sW[i + 1], high, x2, cur, aux, pr, pi);
+                    step32<CPT, 0, false>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
+                    step32<CPT, 1, false>(sT[i + 1], sW[i + 1], high, x2, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
                 }
-                if (i < nl) step_plain<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, pr, pi);
-                int nv = 0;
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) nv += valid[c] ? 1 : 0;
-                n_sum += (unsigned long long)nl * nv;
+                if (i < nl) step32<CPT, 0, false>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
             } else {
-                int i = 0;
                 for (; i + 1 < nl; i += 2) {
-                    step_scaled<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, nsc, valid, pr, pi, n_sum);
-                    step_scaled<CPT, 1>(sT[i + 1], sW[i + 1], high, x2, cur, aux, nsc, valid, pr, pi, n_sum);
+                    step32<CPT, 0, true>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
+                    step32<CPT, 1, true>(sT[i + 1], sW[i + 1], high, x2, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
                 }
-                if (i < nl) step_scaled<CPT, 0>(sT[i], sW[i], high, x2, cur, aux, nsc, valid, pr, pi, n_sum);
+                if (i < nl) step32<CPT, 0, true>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
             }
             // partials of this tile into the compensated accumulators; the sign of the
             // odd-offset partial is (-1) for mirrored chains, and the tile's start parity
@@ -331,6 +317,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 const double im = sg * ((double)si[c] + (double)ci[c]);
                 out[jj[c]] = bad[c] ? make_double2(nan, nan) : make_double2(re, im);
                 n_elem += (unsigned long long)(L + 1 - l0);
+                n_sum += (unsigned long long)(L + 1 - min(lpl[c], L + 1));
             }
         }
     }

@@ -24,17 +24,19 @@
 #include "wg_internal.h"
 
 namespace wg {
-void set_last_error(const std::string &msg);  // wg_capi.cu: text for wigner_last_error_message
+void set_last_error(const std::string &msg, int code);  // wg_capi.cu: text for wigner_last_error_message
 }
 
 namespace {
 
 struct ErrSink {  // g_err = "..." forwards the text to wigner_last_error_message
+    int code = WG_ERR_ARG;
     ErrSink &operator=(const std::string &m) {
-        wg::set_last_error(m);
+        wg::set_last_error(m, code);
         return *this;
     }
-} g_err;
+};
+thread_local ErrSink g_err;
 
 constexpr int kLcap = WG_NOALLOC_LMAX;
 constexpr size_t kN2 = 2 * (size_t)kLcap + 2;  // ln n!, P_i, Q_i: n, i <= 2 l_max + 1
@@ -80,10 +82,12 @@ int device_tables(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
+        g_err.code = WG_ERR_CUDA;
         g_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
         return WG_ERR_CUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) {
+        g_err.code = WG_ERR_DEVICE;
         g_err = "device ordinal beyond the supported range";
         return WG_ERR_DEVICE;
     }
@@ -93,6 +97,7 @@ int device_tables(double **out) {
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
         if (major != 10 || minor != 3) {
+            g_err.code = WG_ERR_DEVICE;
             g_err = "this library is built for sm_103a (GB300)";
             return WG_ERR_DEVICE;
         }
@@ -100,11 +105,13 @@ int device_tables(double **out) {
         double *p = nullptr;
         e = cudaGetSymbolAddress((void **)&p, g_noalloc_tables);
         if (e != cudaSuccess || p == nullptr) {
+            g_err.code = WG_ERR_CUDA;
             g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return WG_ERR_CUDA;
         }
         e = cudaMemcpyToSymbol(g_noalloc_tables, g_host_tables, sizeof(g_host_tables), 0, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
+            g_err.code = WG_ERR_CUDA;
             g_err = std::string("cudaMemcpyToSymbol: ") + cudaGetErrorString(e);
             return WG_ERR_CUDA;
         }
@@ -120,6 +127,7 @@ bool is_aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 extern "C" int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
                                        const wg_c64 *a, const wg_c64 *b, wg_c64 *c_out, void *stream) {
+    g_err.code = WG_ERR_ARG;
     if (l_max < 0 || l_max > kLcap) {
         g_err = "wigner_conv_sum_noalloc: l_max must be in [0, " + std::to_string(kLcap) +
                 "] (its tables live in a fixed array); use wigner_conv_sum for larger l_max";
@@ -152,6 +160,7 @@ extern "C" int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_
                     nullptr};
     const int err = wg::launch_conv_fp64(ca, t, stream);
     if (err != 0) {
+        g_err.code = WG_ERR_CUDA;
         g_err = std::string("conv_fp64 launch: ") + cudaGetErrorString((cudaError_t)err);
         return WG_ERR_CUDA;
     }

@@ -68,6 +68,9 @@ def load():
                 "wigner_built_arch": [],
                 "wigner_fma_peak": [I, I, I, I, P, P, P],
                 "wigner_conv_sum_noalloc": [I, I, I, I, P, P, P, P, P],
+                "wigner_plan_create": [P, P],
+                "wigner_plan_destroy": [P],
+                "wigner_last_error": [],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -76,6 +79,7 @@ def load():
             lib.wigner_error_string.restype = ctypes.c_char_p
             lib.wigner_last_error_message.restype = ctypes.c_char_p
             lib.wigner_batch_plan_destroy.restype = None
+            lib.wigner_plan_destroy.restype = None
             _lib = lib
     return _lib
 
@@ -290,6 +294,34 @@ def wigner_conv_sum_batched(problems, stream=None):
     return outs
 
 
+class WgParams(ctypes.Structure):
+    _fields_ = [("l_max_cap", ctypes.c_int), ("mb_max_cap", ctypes.c_int), ("ms_max_cap", ctypes.c_int),
+                ("n_beta_cap", ctypes.c_int), ("reserve_backward", ctypes.c_int)]
+
+
+class Plan:
+    """Reserve tables (and optionally the adjoints' workspace) so that calls within the
+    caps allocate nothing -- e.g. to capture them in a CUDA graph (wigner_plan_create)."""
+
+    def __init__(self, l_max_cap: int, mb_max_cap: int = 0, ms_max_cap: int = 0, n_beta_cap: int = 0,
+                 reserve_backward: bool = False):
+        lib = load()
+        self._h = ctypes.c_void_p(0)
+        prm = WgParams(l_max_cap, mb_max_cap, ms_max_cap, n_beta_cap, int(reserve_backward))
+        _check(lib.wigner_plan_create(ctypes.byref(self._h), ctypes.byref(prm)))
+
+    def close(self):
+        if self._h:
+            load().wigner_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def wigner_device_status(stream=None) -> int:
     """Synchronise the stream; return (and clear) the library's device status code."""
     return int(load().wigner_device_status(_stream(stream)))
@@ -315,4 +347,5 @@ def exported_symbols():
             "wigner_conv_sum_batched", "wigner_batch_plan_create", "wigner_batch_run",
             "wigner_batch_plan_destroy", "wigner_device_status", "wigner_error_string",
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
-            "wigner_conv_sum_noalloc", "wigner_batch_plan_info"]
+            "wigner_conv_sum_noalloc", "wigner_batch_plan_info", "wigner_plan_create", "wigner_plan_destroy",
+            "wigner_last_error"]

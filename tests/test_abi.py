@@ -76,3 +76,13 @@ def test_binding_rejects_cpu_tensors():
     import torch
     with pytest.raises(ValueError):
         W.wigner_d_table(torch.zeros(3, dtype=torch.float64), 4, 1, 4)
+
+
+def test_plan_and_last_error_validation(lib):
+    assert lib.wigner_plan_create(None, None) == -1
+    assert lib.wigner_last_error() == -1
+    h = ctypes.c_void_p(0)
+    prm = W.WgParams(-1, 0, 0, 0, 0)
+    assert lib.wigner_plan_create(ctypes.byref(h), ctypes.byref(prm)) == -1
+    assert not h.value
+    lib.wigner_plan_destroy(None)  # NULL is accepted

@@ -26,6 +26,9 @@ def W():
 @pytest.fixture(scope="module")
 def batch(W):
     specs = I.batch_instances(n=14, seed=3, l_range=(8, 420), nb_range=(1, 700))
+    for i, sp in enumerate(specs):  # every third FP64 instance uses the split-pipe FP64 form
+        if sp["form"] == 0 and i % 3 == 0:
+            sp["form"] = 2
     a_full = torch.from_numpy(specs[0]["a_full"]).cuda()
     probs = []
     for sp in specs:
@@ -41,7 +44,7 @@ def batch(W):
 
 def _check(outs, probs, refs):
     for (beta, a, b, f), out, ref in zip(probs, outs, refs):
-        if f == 0:
+        if f in (0, 2):
             assert float((out - ref).abs().max()) <= 1e-11
         else:
             rel = float(torch.linalg.vector_norm(out - ref) / max(float(torch.linalg.vector_norm(ref)), 1e-300))
@@ -53,7 +56,7 @@ def test_batched_convenience(W, batch):
     outs = W.wigner_conv_sum_batched([(beta, a, b, f, None) for beta, a, b, f in probs])
     W.check_device_status()
     _check(outs, probs, refs)
-    assert {f for *_, f in probs} == {0, 1}  # the batch mixes both forms
+    assert {f for *_, f in probs} == {0, 1, 2}  # the batch mixes all three forms
 
 
 def test_plan_graph_replay(W, batch):
@@ -76,7 +79,7 @@ def test_plan_graph_replay(W, batch):
     torch.cuda.synchronize()
     ref0 = W.wigner_conv_sum(beta0, a0, b0, form=f0)
     b0.mul_(0.5)
-    tol = 1e-11 if f0 == 0 else 1e-4 * float(torch.linalg.vector_norm(ref0))
+    tol = 1e-11 if f0 in (0, 2) else 1e-4 * float(torch.linalg.vector_norm(ref0))
     assert float((outs[0] - ref0).abs().max()) <= tol
     plan.close()
     W.check_device_status()
