@@ -287,6 +287,9 @@ def run_ours(args):
     fp32x = None
     if not args.skip_fp32x:
         fp32x = _fp32x_block(W, dev, stream, args)
+    grad = None
+    if not args.skip_grad:
+        grad = _grad_block(W, dev, stream, args)
 
     if rank != 0:
         if dist is not None:
@@ -332,6 +335,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "fp64s": fp64s,
         "fp32x": fp32x,
+        "grad": grad,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -371,6 +375,42 @@ def _fp64s_block(W, beta, a, b, out64, stream, args, elems, mean_ms):
             "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                          "note": "algorithmic flops over the FP64 peak; the sum runs on the FP32 pipe"}}
+
+
+def _grad_block(W, dev, stream, args):
+    """Forward and adjoint on the gradient workload (L=2048, m_b<=8, m_sky<=2048, 1024 uniform
+    angles): time of wigner_conv_sum and of wigner_conv_sum_backward (grad_a, grad_b, grad_beta)."""
+    import torch
+    from paper_1002_1050_gb300 import inputs as I
+
+    c = I.CONFIGS["grad_l2048"]
+    L, MB, MS, NB = c["l_max"], c["mb_max"], c["ms_max"], c["n_beta"]
+    beta = torch.from_numpy(I.beta_uniform(NB, 0.01, math.pi - 0.01, c["seed"])).to(dev)
+    a = torch.from_numpy(I.sky_alm(L, MS, c["seed"])).to(dev)
+    b = torch.from_numpy(I.beam_blm(L, MB)).to(dev)
+    T = W.wigner_conv_sum(beta, torch.from_numpy(I.sky_alm(L, MS, c["target_seed"])).to(dev), b)
+    C = W.wigner_conv_sum(beta, a, b)
+    G = 2.0 * (C - T)
+    W.wigner_conv_sum_backward(beta, a, b, C, G)
+    torch.cuda.synchronize()
+    W.check_device_status()
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_f = timed(lambda: W.wigner_conv_sum(beta, a, b, out=C), 2)
+    ms_b = timed(lambda: W.wigner_conv_sum_backward(beta, a, b, C, G), 2)
+    elems = I.n_elements(L, MB, MS, NB)
+    return {"workload": "grad_l2048 (L=2048, m_b<=8, m_sky<=2048, 1024 uniform angles)",
+            "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
+            "forward_evals_per_s": elems / (ms_f / 1e3), "backward_evals_per_s": elems / (ms_b / 1e3)}
 
 
 def _fp32x_block(W, dev, stream, args):
@@ -518,6 +558,7 @@ def main(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--skip-fp32x", action="store_true", help="skip the FP32-form measurement")
     p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
+    p.add_argument("--skip-grad", action="store_true", help="skip the forward/adjoint timing")
     p.add_argument("--fp64s-steps", type=int, default=5)
     p.add_argument("--fp32x-steps", type=int, default=3)
     p.add_argument("--fp32x-n-beta", type=int, default=8192,

@@ -39,7 +39,7 @@ template <int NT, int CPT64, int TL64, int CPT32, int TL32>
 __global__ void __launch_bounds__(NT) batch_kernel(const BatchInst *__restrict__ insts, const int4 *__restrict__ items,
                                                    int n_items, int *counter, Tables T) {
     __shared__ union {
-        SmemFp64v2<TL64> f64;
+        SmemFp64<TL64> f64;
         SmemFp32<TL32> f32;
     } sm;
     __shared__ int s_item;
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchInst *__restrict__
         const int form = insts[w.x].form;
         unsigned long long ne = 0, ns = 0;
         if (form == WG_FP64)
-            conv_fp64v2_item<NT, CPT64, TL64, false>(a, T, w.y, w.z, w.w, sm.f64, ne, ns);
+            conv_fp64_item<NT, CPT64, TL64, false>(a, T, w.y, w.z, w.w, sm.f64, ne, ns);
         else if (form == WG_FP64S)
-            conv_fp64v2_item<NT, CPT64, TL64, true>(a, T, w.y, w.z, w.w, sm.f64, ne, ns);
+            conv_fp64_item<NT, CPT64, TL64, true>(a, T, w.y, w.z, w.w, sm.f64, ne, ns);
         else
             conv_fp32x_item<NT, CPT32, TL32>(a, T, w.y, w.z, w.w, sm.f32, ne, ns);
     }

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "wg_common.cuh"
+#include "wg_conv_fp64.cuh"  // dbl_to_ff
 
 namespace wg {
 
@@ -210,6 +211,238 @@ __global__ void __launch_bounds__(NT, 1) conv_bwd_kernel(ConvBwdArgs A, Tables T
     }
 }
 
+// v -> lane t holds the warp sum of v[t & 15] (float-float; LB values per lane)
+__device__ __forceinline__ void warp_reduce_scatter16_ff(ff (&v)[LB], int lane) {
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const ff send = up ? v[i] : v[i + off];
+            const ff keep = up ? v[i + off] : v[i];
+            const ff got{__shfl_xor_sync(0xffffffffu, send.hi, off), __shfl_xor_sync(0xffffffffu, send.lo, off)};
+            v[i] = ff_add(keep, got);
+        }
+    }
+    const ff got{__shfl_xor_sync(0xffffffffu, v[0].hi, 16), __shfl_xor_sync(0xffffffffu, v[0].lo, 16)};
+    v[0] = ff_add(v[0], got);
+}
+
+// Adjoint kernel with the forward kernels' normalised two-FMA recursion
+// (u^l = d^l / sigma_l, sigma_{l+1} = F2_l sigma_{l-1}; see wg_conv_fp64.cuh): the FP64
+// pipe runs only the recursion; S = sum_beta G d^l (lane partials, the warp
+// reduce-scatter and the warp sums) and the beta term's neighbour sum E accumulate in
+// float-float on the FP32 pipe (~48-bit), and S is scaled back by sigma_l in double.
+template <int TL>
+struct SmemBwd2 {
+    double2 sA[TL];       // (F0', G')  (phase 1: (F0, G))
+    double2 sWd[TL];      // E weights (phase 1: w sqrt(...)), then times sigma_l
+    float4 sWE[TL];       // E weights as float-float
+    long long sThr[TL];   // bit pattern of 1e-30 / sigma_l
+    double sF2[TL];
+    double sSig[TL + 1];
+    float4 sRed[TL / LB][8][LB];  // warp sums of S per l (re hi, lo, im hi, lo), up to 8 warps
+};
+
+template <int NT, int CPT, int TL>
+__global__ void __launch_bounds__(NT) conv_bwd2_kernel(ConvBwdArgs A, Tables T, int n_chunks, int group, int ms_hi,
+                                                       int want_s, int atomic_s, double *partial) {
+    static_assert(TL % LB == 0, "tile must hold whole l-blocks");
+    constexpr int NW = NT / 32;
+    static_assert(NW <= 8, "at most 8 warps");
+    __shared__ SmemBwd2<TL> sm;
+    const int item = blockIdx.x;
+    const int chunk = item % n_chunks;
+    const int grp = item / n_chunks;
+    const int MB1 = A.mb_max + 1;
+    const int MS1 = A.ms_max + 1;
+    const int ncol = MB1 * (ms_hi + 1);
+    const int k_begin = grp * group;
+    const int k_end = min(ncol, k_begin + group);
+    const int L = A.l_max;
+    const int NB = A.n_beta;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool want_e = partial != nullptr;
+
+    int jj[CPT];
+    bool valid[CPT];
+    Angle ang[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        jj[c] = chunk * NT * CPT + c * NT + tid;
+        valid[c] = jj[c] < NB;
+        ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
+        if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
+    }
+
+    for (int k = k_begin; k < k_end; ++k) {
+        const int ms = k / MB1, mb = k - ms * MB1;  // this chain column is (mb, ms)
+        const int l0 = mb > ms ? mb : ms;
+        const bool do_s = want_s && ms <= A.ms_max;
+        const bool do_e = want_e && ms >= 1;
+
+        double u[CPT], up[CPT];
+        ff gr[CPT], gi[CPT], er[CPT], ei[CPT];
+        int nsc[CPT];
+        bool plain[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const Scaled s = seed_value(mb, ms, ang[c], T);
+            u[c] = s.mant;
+            nsc[c] = s.n;
+            plain[c] = s.plain;
+            up[c] = 0.0;
+            er[c] = ei[c] = ff{0.f, 0.f};
+            gr[c] = gi[c] = ff{0.f, 0.f};
+            if (do_s && valid[c]) {
+                const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[((size_t)mb * MS1 + ms) * NB + jj[c]];
+                gr[c] = ff{__double2float_rn(g.x), __double2float_rn(g.x - (double)__double2float_rn(g.x))};
+                gi[c] = ff{__double2float_rn(g.y), __double2float_rn(g.y - (double)__double2float_rn(g.y))};
+            }
+        }
+        double sig_m1 = 0.0, sig_0 = 1.0;
+
+        for (int ts = l0; ts <= L; ts += TL) {
+            __syncthreads();
+            for (int i = tid; i < TL; i += NT) {  // phase 1
+                const int l = ts + i;
+                double f0 = 0.0, g = 0.0, f2 = 0.0;
+                double2 w = make_double2(0.0, 0.0);
+                if (l <= L) {
+                    if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
+                    if (do_e) {
+                        const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * MS1 + (ms - 1)];
+                        const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+                        const double sq = sqrt((double)(l - ms + 1) * (double)(l + ms));
+                        w = make_double2((bv.x * av.x + bv.y * av.y) * sq, (bv.x * av.y - bv.y * av.x) * sq);
+                    }
+                }
+                sm.sA[i] = make_double2(f0, g);
+                sm.sF2[i] = f2;
+                sm.sWd[i] = w;
+            }
+            __syncthreads();
+            if (tid == 0) {  // phase 2: sigma
+                double sm1 = sig_m1, s0 = sig_0;
+                sm.sSig[0] = s0;
+                for (int i = 0; i < TL; ++i) {
+                    const int l = ts + i;
+                    const double nx = (l == l0 || l >= L) ? s0 : sm.sF2[i] * sm1;
+                    sm.sSig[i + 1] = nx;
+                    sm1 = s0;
+                    s0 = nx;
+                }
+                sig_m1 = sm1;
+                sig_0 = s0;
+            }
+            __syncthreads();
+            for (int i = tid; i < TL; i += NT) {  // phase 3
+                const int l = ts + i;
+                const double sg = sm.sSig[i];
+                double2 fg = sm.sA[i];
+                if (l < L) {
+                    const double rho = sg / sm.sSig[i + 1];
+                    fg.x *= rho;
+                    fg.y *= rho;
+                }
+                sm.sA[i] = fg;
+                const double2 w = sm.sWd[i];
+                float4 wf;
+                dbl_to_ff(w.x * sg, wf.x, wf.y);
+                dbl_to_ff(w.y * sg, wf.z, wf.w);
+                sm.sWE[i] = wf;
+                sm.sThr[i] = __double_as_longlong(WG_EPS_SUM / sg);
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int blk = 0; blk < TL / LB; ++blk) {
+                const int lb = ts + blk * LB;
+                if (lb > L) break;  // uniform over the CTA
+                ff sr[LB], si[LB];
+#pragma unroll
+                for (int i = 0; i < LB; ++i) {
+                    const int l = lb + i;
+                    sr[i] = si[i] = ff{0.f, 0.f};
+                    if (l <= L) {  // uniform
+                        const int ti = blk * LB + i;
+                        const float4 we = sm.sWE[ti];
+                        const long long thr = sm.sThr[ti];
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) {
+                            // terms with |d| < 1e-30 are left out, as in the forward sum;
+                            // this also keeps split_ff inside its range (|u| >= 2^-100)
+                            ff uu = split_ff(u[c]);
+                            if (!plain[c] || !abs_ge(u[c], thr)) uu = ff{0.f, 0.f};
+                            if (do_s) {
+                                ff_mac(sr[i], gr[c].hi, gr[c].lo, uu.hi, uu.lo);
+                                ff_mac(si[i], gi[c].hi, gi[c].lo, uu.hi, uu.lo);
+                            }
+                            if (do_e) {
+                                ff_mac(er[c], we.x, we.y, uu.hi, uu.lo);
+                                ff_mac(ei[c], we.z, we.w, uu.hi, uu.lo);
+                            }
+                        }
+                        if (l < L) {
+                            const double2 fg = sm.sA[ti];
+#pragma unroll
+                            for (int c = 0; c < CPT; ++c) {
+                                const double y = fma(fg.x, ang[c].cb, -fg.y);
+                                const double nx = fma(y, u[c], -up[c]);
+                                up[c] = u[c];
+                                u[c] = nx;
+                                if (!plain[c]) scaled_fixup(u[c], up[c], nsc[c], plain[c]);
+                            }
+                        }
+                    }
+                }
+                if (do_s) {
+                    warp_reduce_scatter16_ff(sr, lane);
+                    warp_reduce_scatter16_ff(si, lane);
+                    if (lane < LB) sm.sRed[blk][warp][lane] = make_float4(sr[0].hi, sr[0].lo, si[0].hi, si[0].lo);
+                }
+            }
+            __syncthreads();
+            if (do_s) {
+                for (int i = tid; i < TL; i += NT) {
+                    const int l = ts + i;
+                    if (l > L) continue;
+                    ff re{0.f, 0.f}, im{0.f, 0.f};
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        const float4 v = sm.sRed[i / LB][w][i % LB];
+                        re = ff_add(re, ff{v.x, v.y});
+                        im = ff_add(im, ff{v.z, v.w});
+                    }
+                    const double sg = sm.sSig[i];
+                    const double vr = ((double)re.hi + (double)re.lo) * sg;
+                    const double vi = ((double)im.hi + (double)im.lo) * sg;
+                    double *dst = A.S + 2 * (((size_t)l * MB1 + mb) * MS1 + ms);
+                    if (atomic_s) {
+                        atomicAdd(dst, vr);
+                        atomicAdd(dst + 1, vi);
+                    } else {
+                        dst[0] = vr;
+                        dst[1] = vi;
+                    }
+                }
+            }
+        }
+        if (do_e) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                if (!valid[c]) continue;
+                const size_t o = ((size_t)mb * MS1 + (ms - 1)) * NB + jj[c];
+                const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[o];
+                const double2 cf = reinterpret_cast<const double2 *>(A.c_fwd)[o];
+                const double coef = ((double)(ms - 1) * ang[c].cb - (double)mb) / ang[c].sb;
+                const double vr = coef * cf.x - ((double)er[c].hi + (double)er[c].lo);
+                const double vi = coef * cf.y - ((double)ei[c].hi + (double)ei[c].lo);
+                partial[o] = g.x * vr + g.y * vi;
+            }
+        }
+    }
+}
+
 // grad_beta[j] = sum over columns of partial[col][j] (fixed order); NaN outside (0, pi)
 __global__ void reduce_columns_kernel(const double *partial, int ncol, int n_beta, const double *beta,
                                       double *grad_beta, int *status) {
@@ -296,8 +529,9 @@ int launch_conv_bwd(const ConvBwdArgs &a, const Tables &t, void *stream_) {
         const int group = 4;
         const long long items = (long long)n_chunks * ((ncol + group - 1) / group);
         if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-        conv_bwd_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, stream>>>(a, t, n_chunks, group, ms_hi, want_s ? 1 : 0,
-                                                                          n_chunks > 1 ? 1 : 0, want_e ? a.E : nullptr);
+        conv_bwd2_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, stream>>>(a, t, n_chunks, group, ms_hi,
+                                                                           want_s ? 1 : 0, n_chunks > 1 ? 1 : 0,
+                                                                           want_e ? a.E : nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return (int)e;
     }

@@ -321,7 +321,7 @@ int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
         wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b,
                         (double *)c_out, counters};
         if (form == WG_FP64) return launch_rc(wg::launch_conv_fp64(ca, t, stream), "conv_fp64 launch");
-        if (form == WG_FP64S) return launch_rc(wg::launch_conv_fp64v2(ca, t, stream), "conv_fp64s launch");
+        if (form == WG_FP64S) return launch_rc(wg::launch_conv_fp64s(ca, t, stream), "conv_fp64s launch");
         return launch_rc(wg::launch_conv_fp32x(ca, t, stream), "conv_fp32x launch");
     } catch (const std::bad_alloc &) {
         return fail(WG_ERR_ALLOC, "host allocation failed");

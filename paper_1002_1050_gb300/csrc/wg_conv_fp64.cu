@@ -6,7 +6,7 @@
 
 namespace wg {
 
-template <int NT, int CPT, int TL>
+template <int NT, int CPT, int TL, bool SUM_FF>
 __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
     __shared__ SmemFp64<TL> sm;
     const int item = blockIdx.x;
@@ -16,42 +16,11 @@ __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int
     const int k_begin = grp * group;
     const int k_end = min(ncol, k_begin + group);
     unsigned long long n_elem = 0, n_sum = 0;
-    conv_fp64_item<NT, CPT, TL>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum);
+    conv_fp64_item<NT, CPT, TL, SUM_FF>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum);
     flush_counters(A.counters, n_elem, n_sum);
 }
 
 template <int NT, int CPT, int TL, bool SUM_FF>
-__global__ void __launch_bounds__(NT) conv_fp64v2_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
-    __shared__ SmemFp64v2<TL> sm;
-    const int item = blockIdx.x;
-    const int chunk = item % n_chunks;
-    const int grp = item / n_chunks;
-    const int ncol = (A.mb_max + 1) * (A.ms_max + 1);
-    const int k_begin = grp * group;
-    const int k_end = min(ncol, k_begin + group);
-    unsigned long long n_elem = 0, n_sum = 0;
-    conv_fp64v2_item<NT, CPT, TL, SUM_FF>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum);
-    flush_counters(A.counters, n_elem, n_sum);
-}
-
-template <int NT, int CPT, int TL, bool SUM_FF>
-static int launch_conv_fp64v2_t(const ConvArgs &a, const Tables &t, void *stream, int group) {
-    const int per_chunk = NT * CPT;
-    const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
-    const int ncol = (a.mb_max + 1) * (a.ms_max + 1);
-    const int n_groups = (ncol + group - 1) / group;
-    const long long items = (long long)n_chunks * n_groups;
-    if (items == 0) return 0;
-    if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-    conv_fp64v2_kernel<NT, CPT, TL, SUM_FF><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group);
-    return (int)cudaGetLastError();
-}
-
-int launch_conv_fp64v2(const ConvArgs &a, const Tables &t, void *stream) {
-    return launch_conv_fp64v2_t<256, 2, 128, true>(a, t, stream, 4);
-}
-
-template <int NT, int CPT, int TL>
 static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, int group) {
     const int per_chunk = NT * CPT;
     const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
@@ -60,19 +29,17 @@ static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, 
     const long long items = (long long)n_chunks * n_groups;
     if (items == 0) return 0;
     if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-    conv_fp64_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group);
+    conv_fp64_kernel<NT, CPT, TL, SUM_FF><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group);
     return (int)cudaGetLastError();
+}
+
+int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream) {
+    return launch_conv_fp64_t<256, 2, 128, true>(a, t, stream, 4);
 }
 
 // all-double form: the normalised two-FMA recursion with the sum in FP64 FMAs
 int launch_conv_fp64(const ConvArgs &a, const Tables &t, void *stream) {
-    return launch_conv_fp64v2_t<256, 2, 128, false>(a, t, stream, 4);
-}
-
-// the first all-double kernel (three FP64 operations per step), kept for comparison
-int launch_conv_fp64_plain3(const ConvArgs &a, const Tables &t, void *stream) {
-    // one chunk per 256 angles; columns grouped so the per-angle set-up is amortised
-    return launch_conv_fp64_t<128, 2, 128>(a, t, stream, 4);
+    return launch_conv_fp64_t<256, 2, 128, false>(a, t, stream, 4);
 }
 
 }  // namespace wg

@@ -27,124 +27,6 @@
 
 namespace wg {
 
-template <int TL>
-struct SmemFp64 {
-    double2 sFG[TL];  // (F0, G)
-    double2 sFW[TL];  // (F2, w_re)
-    double sWI[TL];   // w_im
-};
-
-// One work item: chain columns k in [k_begin, k_end) (m_sky-major order) for the
-// angle chunk `chunk` (NT*CPT angles).  Adds the elements evaluated and summed to the
-// counters.  Every thread of the CTA must call it (it synchronises the CTA).
-template <int NT, int CPT, int TL>
-__device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
-                                               int k_end, SmemFp64<TL> &sm, unsigned long long &n_elem,
-                                               unsigned long long &n_sum) {
-    const int MB1 = A.mb_max + 1;
-    const int L = A.l_max;
-    const int NB = A.n_beta;
-    const int tid = threadIdx.x;
-    double2 *sFG = sm.sFG;
-    double2 *sFW = sm.sFW;
-    double *sWI = sm.sWI;
-
-    int jj[CPT];
-    bool valid[CPT];
-    Angle ang[CPT];
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        jj[c] = chunk * NT * CPT + c * NT + tid;
-        valid[c] = jj[c] < NB;
-        ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
-        if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
-    }
-    const long long eps_bits = __double_as_longlong(WG_EPS_SUM);
-
-    for (int k = k_begin; k < k_end; ++k) {
-        const int ms = k / MB1, mb = k - ms * MB1;
-        const int l0 = mb > ms ? mb : ms;
-
-        double cur[CPT], prev[CPT], cre[CPT], cim[CPT];
-        int nsc[CPT];
-        bool plain[CPT], summing[CPT];
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const Scaled s = seed_value(mb, ms, ang[c], T);
-            cur[c] = s.mant;
-            nsc[c] = s.n;
-            plain[c] = s.plain;
-            prev[c] = 0.0;
-            cre[c] = 0.0;
-            cim[c] = 0.0;
-            summing[c] = false;
-        }
-        bool warp_sum = false;
-
-        for (int ts = l0; ts <= L; ts += TL) {
-            __syncthreads();
-            for (int i = tid; i < TL; i += NT) {
-                const int l = ts + i;
-                double f0 = 0.0, g = 0.0, f2 = 0.0, wre = 0.0, wim = 0.0;
-                if (l <= L) {
-                    if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
-                    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
-                    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
-                    wre = bv.x * av.x + bv.y * av.y;  // conj(b) * a
-                    wim = bv.x * av.y - bv.y * av.x;
-                }
-                sFG[i] = make_double2(f0, g);
-                sFW[i] = make_double2(f2, wre);
-                sWI[i] = wim;
-            }
-            __syncthreads();
-            const int nl = min(TL, L + 1 - ts);
-            for (int i = 0; i < nl; ++i) {
-                const double2 fg = sFG[i];
-                const double2 fw = sFW[i];
-                const double wim = sWI[i];
-                // term l: start summing at the first |d| >= eps (plain values only)
-                bool any = false;
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    summing[c] = summing[c] || (plain[c] && abs_ge(cur[c], eps_bits));
-                    any |= summing[c];
-                }
-                if (!warp_sum) warp_sum = __any_sync(0xffffffffu, any);
-                if (warp_sum) {
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c) {
-                        const double wr = summing[c] ? fw.y : 0.0;
-                        const double wi = summing[c] ? wim : 0.0;
-                        cre[c] = fma(wr, cur[c], cre[c]);
-                        cim[c] = fma(wi, cur[c], cim[c]);
-                        n_sum += (summing[c] && valid[c]) ? 1 : 0;
-                    }
-                }
-                if (ts + i < L) {
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c) {
-                        const double y = fma(fg.x, ang[c].cb, -fg.y);
-                        const double nx = fma(y, cur[c], -(fw.x * prev[c]));
-                        prev[c] = cur[c];
-                        cur[c] = nx;
-                        if (!plain[c]) scaled_fixup(cur[c], prev[c], nsc[c], plain[c]);
-                    }
-                }
-            }
-        }
-        double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            if (valid[c]) {
-                const double nan = __longlong_as_double(0x7ff8000000000000LL);
-                out[jj[c]] = ang[c].bad ? make_double2(nan, nan) : make_double2(cre[c], cim[c]);
-                n_elem += (unsigned long long)(L + 1 - l0);
-            }
-        }
-    }
-}
-
 // ===========================================================================
 // The FP64 kernels: two FP64 instructions per recursion step.
 //
@@ -166,7 +48,7 @@ __device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &
 // tables.  The threshold |d| >= 1e-30 of Sec. 4.2.1 becomes |u| >= 1e-30 / sigma_l.
 // ===========================================================================
 template <int TL>
-struct SmemFp64v2 {
+struct SmemFp64 {
     double2 sA[TL];        // (F0', G')   (phase 1: (F0, G))
     double2 sWd[TL];       // w_l = conj(b) a (phase 1), then w_l sigma_l
     float4 sW[TL];         // w_l sigma_l as float-float (re hi, lo, im hi, lo)
@@ -181,8 +63,8 @@ __device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
 }
 
 template <int NT, int CPT, int TL, bool SUM_FF>
-__device__ __forceinline__ void conv_fp64v2_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
-                                                 int k_end, SmemFp64v2<TL> &sm, unsigned long long &n_elem,
+__device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
+                                                 int k_end, SmemFp64<TL> &sm, unsigned long long &n_elem,
                                                  unsigned long long &n_sum) {
     const int MB1 = A.mb_max + 1;
     const int L = A.l_max;

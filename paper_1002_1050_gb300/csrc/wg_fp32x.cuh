@@ -177,20 +177,23 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
 }
 
 // One l-step of CPT chains: term l into the partial of parity PAR, then the
-// difference-form step to l+1.  MASKED: some chain of the warp may still be scaled
-// (value < 2^-64); those add no term, and a chain whose mantissa leaves [2^-64, 2^64)
-// is rescaled (rarely taken branch).  lpl records the l at which a chain turned plain.
+// difference-form step to l+1.  x2s carries x^2 with the sign bit set for mirrored
+// chains (beta > pi/2); the sign selects K1 over K0 with one bitwise operation.
+// MASKED: some chain of the warp may still be scaled (value < 2^-64); those add no
+// term, and a chain whose mantissa leaves [2^-64, 2^64) is rescaled (rarely taken
+// branch).  lpl records the l at which a chain turned plain.
 template <int CPT, int PAR, bool MASKED>
-__device__ __forceinline__ void step32(const float4 tc, const float2 w, const bool (&high)[CPT],
-                                       const float (&x2)[CPT], float (&cur)[CPT], float (&aux)[CPT],
-                                       int (&nsc)[CPT], int (&lpl)[CPT], int l, float (&pr)[2][CPT],
-                                       float (&pi)[2][CPT]) {
+__device__ __forceinline__ void step32(const float4 tc, const float2 w, const float (&x2s)[CPT], float (&cur)[CPT],
+                                       float (&aux)[CPT], int (&nsc)[CPT], int (&lpl)[CPT], int l,
+                                       float (&pr)[2][CPT], float (&pi)[2][CPT]) {
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
         const float cm = (!MASKED || nsc[c] == 0) ? cur[c] : 0.f;
         pr[PAR][c] = fmaf(w.x, cm, pr[PAR][c]);
         pi[PAR][c] = fmaf(w.y, cm, pi[PAR][c]);
-        const float coef = fmaf(tc.x, x2[c], high[c] ? tc.w : tc.z);
+        const int hm = __float_as_int(x2s[c]) >> 31;  // all ones for a mirrored chain
+        const float kk = __int_as_float((__float_as_int(tc.z) & ~hm) | (__float_as_int(tc.w) & hm));
+        const float coef = fmaf(tc.x, fabsf(x2s[c]), kk);
         aux[c] = fmaf(tc.y, aux[c], coef * cur[c]);
         cur[c] = cur[c] + aux[c];
         if (MASKED) {
@@ -225,7 +228,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
 
     int jj[CPT];
     bool valid[CPT], high[CPT], bad[CPT];
-    float x2[CPT];
+    float x2s[CPT];
     Angle32 ang[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
@@ -235,7 +238,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
         bad[c] = ang[c].bad;
         if (valid[c] && bad[c]) raise_status(T.status, WG_DEVERR_BETA);
         high[c] = ang[c].high;
-        x2[c] = ang[c].x2;
+        x2s[c] = high[c] ? -ang[c].x2 : ang[c].x2;
     }
 
     for (int k = k_begin; k < k_end; ++k) {
@@ -286,16 +289,16 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             int i = 0;
             if (warp_plain) {  // every chain of the warp is a plain float from here on
                 for (; i + 1 < nl; i += 2) {
-                    step32<CPT, 0, false>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
-                    step32<CPT, 1, false>(sT[i + 1], sW[i + 1], high, x2, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
+                    step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
+                    step32<CPT, 1, false>(sT[i + 1], sW[i + 1], x2s, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
                 }
-                if (i < nl) step32<CPT, 0, false>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
+                if (i < nl) step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
             } else {
                 for (; i + 1 < nl; i += 2) {
-                    step32<CPT, 0, true>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
-                    step32<CPT, 1, true>(sT[i + 1], sW[i + 1], high, x2, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
+                    step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
+                    step32<CPT, 1, true>(sT[i + 1], sW[i + 1], x2s, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
                 }
-                if (i < nl) step32<CPT, 0, true>(sT[i], sW[i], high, x2, cur, aux, nsc, lpl, ts + i, pr, pi);
+                if (i < nl) step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
             }
             // partials of this tile into the compensated accumulators; the sign of the
             // odd-offset partial is (-1) for mirrored chains, and the tile's start parity

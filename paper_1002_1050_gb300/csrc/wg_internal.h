@@ -65,8 +65,7 @@ struct ConvBwdArgs {
 int launch_dtable_fp64(const DTableArgs &a, const Tables &t, void *stream);
 int launch_dtable_fp32x(const DTableArgs &a, const Tables &t, void *stream);
 int launch_conv_fp64(const ConvArgs &a, const Tables &t, void *stream);
-int launch_conv_fp64v2(const ConvArgs &a, const Tables &t, void *stream);
-int launch_conv_fp64_plain3(const ConvArgs &a, const Tables &t, void *stream);
+int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream);
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream);
 int launch_dtable_bwd(const DTableBwdArgs &a, const Tables &t, void *stream);
 int launch_conv_bwd(const ConvBwdArgs &a, const Tables &t, void *stream);
