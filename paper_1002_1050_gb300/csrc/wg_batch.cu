@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchInst *__restrict__
                                                    int n_items, int *counter, Tables T) {
     __shared__ union {
         SmemFp64<TL64> f64;
-        SmemFp32<TL32> f32;
+        SmemFp32<NT, CPT32, TL32> f32;
     } sm;
     __shared__ int s_item;
     for (;;) {

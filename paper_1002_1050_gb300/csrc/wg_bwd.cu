@@ -13,7 +13,8 @@
 // no d-table is stored.
 //
 // Kernel layout: as the forward kernel (column group x angle chunk per CTA, CPT chains
-// per thread).  For each column (mb, ms') the CTA runs the chains and
+// per thread, the normalised two-FMA recursion).  For each column (mb, ms') the CTA
+// runs the chains and, in float-float on the FP32 pipe,
 //   * accumulates, per chain, E for column (mb, ms'-1) from the weights of that column;
 //   * forms S[l] = sum over the CTA's angles of G d^l: each lane sums its CPT chains,
 //     a warp reduce-scatter over blocks of 16 l (shuffles) leaves one warp sum per l,
@@ -29,187 +30,6 @@
 namespace wg {
 
 constexpr int LB = 16;  // l-block of the warp reduce-scatter
-
-// v[0..15] per lane -> lane t holds sum over the warp of v[t & 15] in v[0]
-__device__ __forceinline__ void warp_reduce_scatter16(double (&v)[LB], int lane) {
-#pragma unroll
-    for (int off = 8; off >= 1; off >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < off; ++i) {
-            const double send = up ? v[i] : v[i + off];
-            const double keep = up ? v[i + off] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
-}
-
-template <int NT, int CPT, int TL>
-__global__ void __launch_bounds__(NT, 1) conv_bwd_kernel(ConvBwdArgs A, Tables T, int n_chunks, int group,
-                                                      int ms_hi, int want_s, int atomic_s, double *partial) {
-    static_assert(TL % LB == 0, "tile must hold whole l-blocks");
-    constexpr int NW = NT / 32;
-    const int item = blockIdx.x;
-    const int chunk = item % n_chunks;
-    const int grp = item / n_chunks;
-    const int MB1 = A.mb_max + 1;
-    const int MS1 = A.ms_max + 1;
-    const int ncol = MB1 * (ms_hi + 1);
-    const int k_begin = grp * group;
-    const int k_end = min(ncol, k_begin + group);
-    const int L = A.l_max;
-    const int NB = A.n_beta;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool want_e = partial != nullptr;
-
-    __shared__ double2 sFG[TL];        // (F0, G)
-    __shared__ double sF2[TL];
-    __shared__ double2 sWE[TL];        // weights of column (mb, ms'-1) times sqrt((l-ms'+1)(l+ms'))
-    __shared__ double2 sRed[TL / LB][NW][LB];
-
-    int jj[CPT];
-    bool valid[CPT];
-    Angle ang[CPT];
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        jj[c] = chunk * NT * CPT + c * NT + tid;
-        valid[c] = jj[c] < NB;
-        ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
-        if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
-    }
-
-    for (int k = k_begin; k < k_end; ++k) {
-        const int ms = k / MB1, mb = k - ms * MB1;  // this chain column is (mb, ms)
-        const int l0 = mb > ms ? mb : ms;
-        const bool do_s = want_s && ms <= A.ms_max;
-        const bool do_e = want_e && ms >= 1;
-
-        double cur[CPT], prev[CPT], ere[CPT], eim[CPT], gre[CPT], gim[CPT];
-        int nsc[CPT];
-        bool plain[CPT];
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const Scaled s = seed_value(mb, ms, ang[c], T);
-            cur[c] = s.mant;
-            nsc[c] = s.n;
-            plain[c] = s.plain;
-            prev[c] = 0.0;
-            ere[c] = 0.0;
-            eim[c] = 0.0;
-            gre[c] = 0.0;
-            gim[c] = 0.0;
-            if (do_s && valid[c]) {
-                const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[((size_t)mb * MS1 + ms) * NB + jj[c]];
-                gre[c] = g.x;
-                gim[c] = g.y;
-            }
-        }
-
-        for (int ts = l0; ts <= L; ts += TL) {
-            __syncthreads();
-            for (int i = tid; i < TL; i += NT) {
-                const int l = ts + i;
-                double f0 = 0.0, g = 0.0, f2 = 0.0, wre = 0.0, wim = 0.0;
-                if (l <= L) {
-                    if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
-                    if (do_e) {
-                        const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * MS1 + (ms - 1)];
-                        const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
-                        const double sq = sqrt((double)(l - ms + 1) * (double)(l + ms));
-                        wre = (bv.x * av.x + bv.y * av.y) * sq;
-                        wim = (bv.x * av.y - bv.y * av.x) * sq;
-                    }
-                }
-                sFG[i] = make_double2(f0, g);
-                sF2[i] = f2;
-                sWE[i] = make_double2(wre, wim);
-            }
-            __syncthreads();
-#pragma unroll 1
-            for (int blk = 0; blk < TL / LB; ++blk) {
-                const int lb = ts + blk * LB;
-                if (lb > L) break;  // uniform over the CTA
-                double sr[LB], si[LB];
-#pragma unroll
-                for (int i = 0; i < LB; ++i) {
-                    const int l = lb + i;
-                    sr[i] = 0.0;
-                    si[i] = 0.0;
-                    if (l <= L) {  // uniform
-                        const int ti = blk * LB + i;
-#pragma unroll
-                        for (int c = 0; c < CPT; ++c) {
-                            const double dv = plain[c] ? cur[c] : 0.0;  // scaled values are < 2^-900
-                            if (do_s) {
-                                sr[i] = fma(gre[c], dv, sr[i]);
-                                si[i] = fma(gim[c], dv, si[i]);
-                            }
-                            if (do_e) {
-                                const double2 we = sWE[ti];
-                                ere[c] = fma(we.x, dv, ere[c]);
-                                eim[c] = fma(we.y, dv, eim[c]);
-                            }
-                        }
-                        if (l < L) {
-                            const double2 fg = sFG[ti];
-                            const double f2 = sF2[ti];
-#pragma unroll
-                            for (int c = 0; c < CPT; ++c) {
-                                const double y = fma(fg.x, ang[c].cb, -fg.y);
-                                const double nx = fma(y, cur[c], -(f2 * prev[c]));
-                                prev[c] = cur[c];
-                                cur[c] = nx;
-                                if (!plain[c]) scaled_fixup(cur[c], prev[c], nsc[c], plain[c]);
-                            }
-                        }
-                    }
-                }
-                if (do_s) {
-                    warp_reduce_scatter16(sr, lane);
-                    warp_reduce_scatter16(si, lane);
-                    if (lane < LB) sRed[blk][warp][lane] = make_double2(sr[0], si[0]);
-                }
-            }
-            __syncthreads();
-            if (do_s) {
-                for (int i = tid; i < TL; i += NT) {
-                    const int l = ts + i;
-                    if (l > L) continue;
-                    double re = 0.0, im = 0.0;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        const double2 v = sRed[i / LB][w][i % LB];
-                        re += v.x;
-                        im += v.y;
-                    }
-                    double *dst = A.S + 2 * (((size_t)l * MB1 + mb) * MS1 + ms);
-                    if (atomic_s) {
-                        atomicAdd(dst, re);
-                        atomicAdd(dst + 1, im);
-                    } else {
-                        dst[0] = re;
-                        dst[1] = im;
-                    }
-                }
-            }
-        }
-        // beta term for column (mb, ms-1): Re conj(G) (coef C - E), coef = ((ms-1) cos b - mb)/sin b
-        if (do_e) {
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                if (!valid[c]) continue;
-                const size_t o = ((size_t)mb * MS1 + (ms - 1)) * NB + jj[c];
-                const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[o];
-                const double2 cf = reinterpret_cast<const double2 *>(A.c_fwd)[o];
-                const double coef = ((double)(ms - 1) * ang[c].cb - (double)mb) / ang[c].sb;
-                const double vr = coef * cf.x - ere[c];
-                const double vi = coef * cf.y - eim[c];
-                partial[o] = g.x * vr + g.y * vi;
-            }
-        }
-    }
-}
 
 // v -> lane t holds the warp sum of v[t & 15] (float-float; LB values per lane)
 __device__ __forceinline__ void warp_reduce_scatter16_ff(ff (&v)[LB], int lane) {
@@ -229,12 +49,12 @@ __device__ __forceinline__ void warp_reduce_scatter16_ff(ff (&v)[LB], int lane) 
 }
 
 // Adjoint kernel with the forward kernels' normalised two-FMA recursion
-// (u^l = d^l / sigma_l, sigma_{l+1} = F2_l sigma_{l-1}; see wg_conv_fp64.cuh): the FP64
+// (u^l = d^l / sigma_l, sigma_{l+1} = F2_l sigma_{l-1}, as in wg_conv_fp64.cuh): the FP64
 // pipe runs only the recursion; S = sum_beta G d^l (lane partials, the warp
 // reduce-scatter and the warp sums) and the beta term's neighbour sum E accumulate in
 // float-float on the FP32 pipe (~48-bit), and S is scaled back by sigma_l in double.
 template <int TL>
-struct SmemBwd2 {
+struct SmemBwd {
     double2 sA[TL];       // (F0', G')  (phase 1: (F0, G))
     double2 sWd[TL];      // E weights (phase 1: w sqrt(...)), then times sigma_l
     float4 sWE[TL];       // E weights as float-float
@@ -245,12 +65,12 @@ struct SmemBwd2 {
 };
 
 template <int NT, int CPT, int TL>
-__global__ void __launch_bounds__(NT) conv_bwd2_kernel(ConvBwdArgs A, Tables T, int n_chunks, int group, int ms_hi,
+__global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, int n_chunks, int group, int ms_hi,
                                                        int want_s, int atomic_s, double *partial) {
     static_assert(TL % LB == 0, "tile must hold whole l-blocks");
     constexpr int NW = NT / 32;
     static_assert(NW <= 8, "at most 8 warps");
-    __shared__ SmemBwd2<TL> sm;
+    __shared__ SmemBwd<TL> sm;
     const int item = blockIdx.x;
     const int chunk = item % n_chunks;
     const int grp = item / n_chunks;
@@ -529,7 +349,7 @@ int launch_conv_bwd(const ConvBwdArgs &a, const Tables &t, void *stream_) {
         const int group = 4;
         const long long items = (long long)n_chunks * ((ncol + group - 1) / group);
         if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-        conv_bwd2_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, stream>>>(a, t, n_chunks, group, ms_hi,
+        conv_bwd_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, stream>>>(a, t, n_chunks, group, ms_hi,
                                                                            want_s ? 1 : 0, n_chunks > 1 ? 1 : 0,
                                                                            want_e ? a.E : nullptr);
         e = cudaGetLastError();

@@ -8,7 +8,7 @@ namespace wg {
 
 template <int NT, int CPT, int TL>
 __global__ void __launch_bounds__(NT) conv_fp32x_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
-    __shared__ SmemFp32<TL> sm;
+    __shared__ SmemFp32<NT, CPT, TL> sm;
     const int item = blockIdx.x;
     const int chunk = item % n_chunks;
     const int grp = item / n_chunks;

@@ -1,11 +1,12 @@
-// wg_fp32x.cu -- the FP32 form: recursion body in float with an int32 exponent carry.
+// wg_fp32x.cuh -- the FP32 form: recursion body in float with an int32 exponent carry.
 //
-// Precision design (see the FP32 accuracy study recorded with the project):
-//  * Seeds (Eqs. ini1-ini2, logstart) in double-double, split into a float mantissa
+// Precision design:
+//  * Seeds (Eqs. ini1-ini2, logstart) in float-float on the FP32 pipe from float-float
+//    tables of ln n! and per-angle half-angle logarithms, split into a float mantissa
 //    and an int32 count n of factors 2^64:  value = mant * 2^(64 n).
-//  * The coefficient tables of Sec. 4.2.2 (F0, F0*F1, F2) are built in double and
-//    combined, still in double, into the coefficients of a difference form of
-//    Eq. lrec before rounding to float:
+//  * The coefficients of Sec. 4.2.2 (F0, F0*F1, F2) are built in float-float from the
+//    float-float tables P, Q, 1/(l(l+1)), (l+1)/l and combined, still in float-float,
+//    into the coefficients of a difference form of Eq. lrec before rounding to float:
 //        Delta_{l+1} = F2_l Delta_l + (K_l - 2 F0_l x^2) d^l,   d^{l+1} = d^l + Delta_{l+1},
 //    with Delta_l = d^l - d^{l-1}, x^2 = sin^2(beta/2), K_l = F0_l (1 - F1_l) - 1 - F2_l.
 //    Straight float recursion loses all accuracy near the poles (cos beta rounds to
@@ -13,12 +14,14 @@
 //    (x^2, K_l) carry their own relative precision.  For beta > pi/2 the same form runs
 //    on e^l = (-1)^l d^l, which obeys Eq. lrec with cos beta -> -cos beta and
 //    F1 -> -F1: x^2 = cos^2(beta/2), K_l = F0_l (1 + F1_l) - 1 - F2_l.
-//  * Scaled mode while the value is below 2^-64: mantissa kept in [2^-64, 2^64] by
-//    joint rescaling of (d, Delta) on the integer pipe; plain floats after that.
+//  * Scaled mode while the value is below 2^-64: every fourth step the pair (d, Delta)
+//    is scaled jointly by 2^-64 or 2^64 when the mantissa has left [2^-64, 2^64); a
+//    chain whose value has reached 2^-64 turns into a plain float at the next l-tile.
+//    A warp whose chains are all plain runs the step without any of this.
 //  * Sum C = sum_l w_l d^l in float: terms go into two per-parity partial sums
 //    (even/odd l, so the (-1)^l of the mirrored chains is applied once per tile), and
 //    each tile's partials are added into a Neumaier-compensated float accumulator.
-//    Terms start with the first plain value (|d| >= 2^-64; the paper's 1e-30 skip
+//    Terms start once the value reaches 2^-64 (the paper's 1e-30 skip of Sec. 4.2.1
 //    drops terms below the FP32 form's resolution anyway).
 #pragma once
 
@@ -179,16 +182,16 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
 // One l-step of CPT chains: term l into the partial of parity PAR, then the
 // difference-form step to l+1.  x2s carries x^2 with the sign bit set for mirrored
 // chains (beta > pi/2); the sign selects K1 over K0 with one bitwise operation.
-// MASKED: some chain of the warp may still be scaled (value < 2^-64); those add no
-// term, and a chain whose mantissa leaves [2^-64, 2^64) is rescaled (rarely taken
-// branch).  lpl records the l at which a chain turned plain.
+// MASKED: some chain of the warp is still scaled; its term is cur * sp, where
+// sp = 2^(64 n) for the count n of 2^64 factors (1 for a plain chain, 2^-64 for n = -1,
+// 0 below: those terms are < 2^-64 |w|).
 template <int CPT, int PAR, bool MASKED>
 __device__ __forceinline__ void step32(const float4 tc, const float2 w, const float (&x2s)[CPT], float (&cur)[CPT],
-                                       float (&aux)[CPT], int (&nsc)[CPT], int (&lpl)[CPT], int l,
-                                       float (&pr)[2][CPT], float (&pi)[2][CPT]) {
+                                       float (&aux)[CPT], const float (&sp)[CPT], float (&pr)[2][CPT],
+                                       float (&pi)[2][CPT]) {
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        const float cm = (!MASKED || nsc[c] == 0) ? cur[c] : 0.f;
+        const float cm = MASKED ? cur[c] * sp[c] : cur[c];
         pr[PAR][c] = fmaf(w.x, cm, pr[PAR][c]);
         pi[PAR][c] = fmaf(w.y, cm, pi[PAR][c]);
         const int hm = __float_as_int(x2s[c]) >> 31;  // all ones for a mirrored chain
@@ -196,66 +199,94 @@ __device__ __forceinline__ void step32(const float4 tc, const float2 w, const fl
         const float coef = fmaf(tc.x, fabsf(x2s[c]), kk);
         aux[c] = fmaf(tc.y, aux[c], coef * cur[c]);
         cur[c] = cur[c] + aux[c];
-        if (MASKED) {
-            const int e = (__float_as_int(cur[c]) >> 23) & 0xff;
-            if (nsc[c] != 0 && (unsigned)(e - 63) > 127u) {
-                fixup32(cur[c], aux[c], nsc[c]);
-                if (nsc[c] == 0) lpl[c] = l + 1;
-            }
-        }
     }
 }
 
-template <int TL>
+// Rescaling of the scaled chains, run every RESCALE_EVERY steps of a masked tile: a
+// mantissa at or above 2^64 is scaled by 2^-64 (n += 1), one of a scaled chain below
+// 2^-64 by 2^64 (n -= 1), jointly with aux; then sp = 2^(64 n) (0 for n <= -2).  No
+// branch.  Between two calls the mantissa changes by less than 2^60: the ratio of
+// consecutive values is at most |F0 (cos b - F1)| + 1 <= 2 (l0 + 1) / (k + 1) + 1 at
+// l = l0 + k (largest for m_b = m_sky = l0), so four steps from l0 <= 32767 grow it by
+// at most 2^64 / 24, and a mantissa left in [2^-64, 2^64) stays a normal float.
+constexpr int RESCALE_EVERY = 4;
+template <int CPT>
+__device__ __forceinline__ void rescale32(float (&cur)[CPT], float (&aux)[CPT], int (&nsc)[CPT], float (&sp)[CPT]) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        const float m = fabsf(cur[c]);
+        const bool dn = m >= 0x1p64f;
+        const bool up = (m < 0x1p-64f) && (nsc[c] != 0);
+        const float f = dn ? 0x1p-64f : (up ? 0x1p64f : 1.0f);
+        cur[c] *= f;
+        aux[c] *= f;
+        nsc[c] += (int)dn - (int)up;
+        sp[c] = __int_as_float(max(0, 127 + 64 * nsc[c]) << 23);
+    }
+}
+
+// Shared memory of one FP32-form CTA: the l-tile's coefficients and weights, and the
+// per-chain state that is touched once per column or per tile (kept out of registers
+// so that more warps fit on an SM): the seeds' half-angle logarithms and flags, and
+// the Neumaier-compensated sums.
+template <int NT, int CPT, int TL>
 struct SmemFp32 {
-    float4 sT[TL];
-    float2 sW[TL];
+    float4 sT[TL];          // (A = -2 F0, F2, K0, K1) per l
+    float2 sW[TL];          // (w_re, w_im) per l
+    float4 sLog[CPT][NT];   // (ln cos(b/2) hi, lo, ln sin(b/2) hi, lo)
+    int sFlag[CPT][NT];     // bit 0: bad angle, 1: mirrored, 2: cos(b/2) = 0, 3: sin(b/2) = 0
+    float4 sAcc[CPT][NT];   // compensated sums (re, re carry, im, im carry)
 };
 
 // One work item of the FP32 form: chain columns k in [k_begin, k_end) (m_sky-major
 // order) for the angle chunk `chunk` (NT*CPT angles).  Every thread of the CTA calls it.
 template <int NT, int CPT, int TL>
 __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
-                                                int k_end, SmemFp32<TL> &sm, unsigned long long &n_elem,
+                                                int k_end, SmemFp32<NT, CPT, TL> &sm, unsigned long long &n_elem,
                                                 unsigned long long &n_sum) {
-    static_assert(TL % 2 == 0, "tile length must be even (parity of l is tracked per tile)");
+    static_assert(TL % 4 == 0, "tile length must be a multiple of 4 (parity of l and the rescale period)");
     const int MB1 = A.mb_max + 1;
     const int L = A.l_max;
     const int NB = A.n_beta;
     const int tid = threadIdx.x;
+    const int j0 = chunk * NT * CPT + tid;  // angle of chain c: j0 + c * NT
     float4 *sT = sm.sT;
     float2 *sW = sm.sW;
 
-    int jj[CPT];
-    bool valid[CPT], high[CPT], bad[CPT];
-    float x2s[CPT];
-    Angle32 ang[CPT];
+    float x2s[CPT];  // x^2 with the sign bit set for a mirrored chain
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        jj[c] = chunk * NT * CPT + c * NT + tid;
-        valid[c] = jj[c] < NB;
-        ang[c] = make_angle32(valid[c] ? A.beta[jj[c]] : 1.0);
-        bad[c] = ang[c].bad;
-        if (valid[c] && bad[c]) raise_status(T.status, WG_DEVERR_BETA);
-        high[c] = ang[c].high;
-        x2s[c] = high[c] ? -ang[c].x2 : ang[c].x2;
+        const bool valid = j0 + c * NT < NB;
+        const Angle32 t = make_angle32(valid ? A.beta[j0 + c * NT] : 1.0);
+        if (valid && t.bad) raise_status(T.status, WG_DEVERR_BETA);
+        x2s[c] = t.high ? -t.x2 : t.x2;
+        sm.sLog[c][tid] = make_float4(t.lnc.hi, t.lnc.lo, t.lns.hi, t.lns.lo);
+        sm.sFlag[c][tid] = (t.bad ? 1 : 0) | (t.high ? 2 : 0) | (t.c_zero ? 4 : 0) | (t.s_zero ? 8 : 0);
     }
 
     for (int k = k_begin; k < k_end; ++k) {
         const int ms = k / MB1, mb = k - ms * MB1;
         const int l0 = mb > ms ? mb : ms;
 
-        float cur[CPT], aux[CPT], pr[2][CPT], pi[2][CPT], sr[CPT], cr[CPT], si[CPT], ci[CPT];
-        int nsc[CPT], lpl[CPT];
+        float cur[CPT], aux[CPT], sp[CPT], pr[2][CPT], pi[2][CPT];
+        int nsc[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-            const Seed32 s = seed32(mb, ms, ang[c], T);
+            const float4 lg = sm.sLog[c][tid];
+            const int fl = sm.sFlag[c][tid];
+            Angle32 t;
+            t.lnc = ff{lg.x, lg.y};
+            t.lns = ff{lg.z, lg.w};
+            t.c_zero = (fl & 4) != 0;
+            t.s_zero = (fl & 8) != 0;
+            const Seed32 s = seed32(mb, ms, t, T);
             // mirrored chains start from e^{l0} = (-1)^{l0} d^{l0}
-            cur[c] = (high[c] && (l0 & 1)) ? -s.mant : s.mant;
+            cur[c] = ((fl & 2) && (l0 & 1)) ? -s.mant : s.mant;
             aux[c] = cur[c];  // Delta_{l0} = d^{l0} - d^{l0-1} = d^{l0}
             nsc[c] = s.n;
-            lpl[c] = (s.n == 0) ? l0 : L + 1;
-            sr[c] = cr[c] = si[c] = ci[c] = 0.f;
+            sp[c] = (s.n == 0) ? 1.0f : 0.0f;  // a scaled seed has n <= -2
+            if (s.n == 0 && j0 + c * NT < NB) n_sum += (unsigned long long)(L + 1 - l0);
+            sm.sAcc[c][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         bool warp_plain = false;
 
@@ -281,46 +312,70 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             }
             const int nl = min(TL, L + 1 - ts);
             if (!warp_plain) {
+                // a chain with n = -1 (value >= 2^-64) becomes a plain float here, at the
+                // tile boundary (exact: a power-of-two scaling of normal floats)
                 bool p = true;
 #pragma unroll
-                for (int c = 0; c < CPT; ++c) p = p && (nsc[c] == 0);
+                for (int c = 0; c < CPT; ++c) {
+                    if (nsc[c] == -1) {
+                        cur[c] *= 0x1p-64f;
+                        aux[c] *= 0x1p-64f;
+                        nsc[c] = 0;
+                        sp[c] = 1.0f;
+                        if (j0 + c * NT < NB) n_sum += (unsigned long long)(L + 1 - ts);
+                    }
+                    p = p && (nsc[c] == 0);
+                }
                 warp_plain = __all_sync(0xffffffffu, p);
             }
             int i = 0;
             if (warp_plain) {  // every chain of the warp is a plain float from here on
                 for (; i + 1 < nl; i += 2) {
-                    step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
-                    step32<CPT, 1, false>(sT[i + 1], sW[i + 1], x2s, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
+                    step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
+                    step32<CPT, 1, false>(sT[i + 1], sW[i + 1], x2s, cur, aux, sp, pr, pi);
                 }
-                if (i < nl) step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
+                if (i < nl) step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
             } else {
-                for (; i + 1 < nl; i += 2) {
-                    step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
-                    step32<CPT, 1, true>(sT[i + 1], sW[i + 1], x2s, cur, aux, nsc, lpl, ts + i + 1, pr, pi);
+                static_assert(RESCALE_EVERY == 4, "the masked loop below is unrolled by four");
+                for (; i + 3 < nl; i += 4) {
+                    step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
+                    step32<CPT, 1, true>(sT[i + 1], sW[i + 1], x2s, cur, aux, sp, pr, pi);
+                    step32<CPT, 0, true>(sT[i + 2], sW[i + 2], x2s, cur, aux, sp, pr, pi);
+                    step32<CPT, 1, true>(sT[i + 3], sW[i + 3], x2s, cur, aux, sp, pr, pi);
+                    rescale32(cur, aux, nsc, sp);
                 }
-                if (i < nl) step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, nsc, lpl, ts + i, pr, pi);
+                if (i < nl) {
+                    step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
+                    if (i + 1 < nl) step32<CPT, 1, true>(sT[i + 1], sW[i + 1], x2s, cur, aux, sp, pr, pi);
+                    if (i + 2 < nl) step32<CPT, 0, true>(sT[i + 2], sW[i + 2], x2s, cur, aux, sp, pr, pi);
+                    rescale32(cur, aux, nsc, sp);
+                }
             }
-            // partials of this tile into the compensated accumulators; the sign of the
-            // odd-offset partial is (-1) for mirrored chains, and the tile's start parity
-            // (that of l0, as TL is even) is applied at the end
+            // partials of this tile into the compensated sums; the sign of the odd-offset
+            // partial is (-1) for mirrored chains, and the tile's start parity (that of
+            // l0, as TL is even) is applied at the end
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
-                const float sg = high[c] ? -1.f : 1.f;
-                neumaier_add(sr[c], cr[c], pr[0][c] + sg * pr[1][c]);
-                neumaier_add(si[c], ci[c], pi[0][c] + sg * pi[1][c]);
+                const float sg = (__float_as_int(x2s[c]) < 0) ? -1.f : 1.f;
+                float4 acc = sm.sAcc[c][tid];
+                neumaier_add(acc.x, acc.y, pr[0][c] + sg * pr[1][c]);
+                neumaier_add(acc.z, acc.w, pi[0][c] + sg * pi[1][c]);
+                sm.sAcc[c][tid] = acc;
             }
         }
         double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-            if (valid[c]) {
-                const double sg = (high[c] && (l0 & 1)) ? -1.0 : 1.0;
+            const int j = j0 + c * NT;
+            if (j < NB) {
+                const int fl = sm.sFlag[c][tid];
+                const float4 acc = sm.sAcc[c][tid];
+                const double sg = ((fl & 2) && (l0 & 1)) ? -1.0 : 1.0;
                 const double nan = __longlong_as_double(0x7ff8000000000000LL);
-                const double re = sg * ((double)sr[c] + (double)cr[c]);
-                const double im = sg * ((double)si[c] + (double)ci[c]);
-                out[jj[c]] = bad[c] ? make_double2(nan, nan) : make_double2(re, im);
+                const double re = sg * ((double)acc.x + (double)acc.y);
+                const double im = sg * ((double)acc.z + (double)acc.w);
+                out[j] = (fl & 1) ? make_double2(nan, nan) : make_double2(re, im);
                 n_elem += (unsigned long long)(L + 1 - l0);
-                n_sum += (unsigned long long)(L + 1 - min(lpl[c], L + 1));
             }
         }
     }
