@@ -455,7 +455,7 @@ def _fp32x_block(W, dev, stream, args):
     torch.cuda.empty_cache()
     return {"workload": f"conv_fp32x_l8192 (L=8192, m_b<=16, m_sky<=8192, {beta.numel()} Gauss-Legendre angles)",
             "value": n_elem / (ms_full / 1e3), "unit": "evals/s", "ms_per_launch": ms_full,
-            "dtype": "f32 recursion + int32 exponent carry, f64 seeds/tables, compensated f32 sums",
+            "dtype": "f32 recursion + int32 exponent carry, float-float seeds and coefficients, compensated f32 sums",
             "rel_l2_vs_fp64_kernel": rel, "error_subset": "every 16th angle (512 of 8192)",
             "speedup_vs_fp64_kernel": ms64 / ms32, "speedup_subset_ms": {"fp64": ms64, "fp32x": ms32},
             "roofline": {"bound": "alu", "pipe": "fp32_fma", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,

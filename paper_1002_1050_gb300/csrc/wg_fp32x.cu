@@ -33,7 +33,7 @@ static int launch_conv_fp32x_t(const ConvArgs &a, const Tables &t, void *stream,
 }
 
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream) {
-    return launch_conv_fp32x_t<128, 4, 64>(a, t, stream, 16);
+    return launch_conv_fp32x_t<128, 4, 128>(a, t, stream, 16);
 }
 
 // ---------------------------------------------------------------------------

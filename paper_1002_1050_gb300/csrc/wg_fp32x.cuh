@@ -179,30 +179,35 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
     s = t;
 }
 
-// One l-step of CPT chains: term l into the partial of parity PAR, then the
-// difference-form step to l+1.  x2s carries x^2 with the sign bit set for mirrored
-// chains (beta > pi/2); the sign selects K1 over K0 with one bitwise operation.
-// MASKED: some chain of the warp is still scaled; its term is cur * sp, where
-// sp = 2^(64 n) for the count n of 2^64 factors (1 for a plain chain, 2^-64 for n = -1,
-// 0 below: those terms are < 2^-64 |w|).
-template <int CPT, int PAR, bool MASKED>
-__device__ __forceinline__ void step32(const float4 tc, const float2 w, const float (&x2s)[CPT], float (&cur)[CPT],
-                                       float (&aux)[CPT], const float (&sp)[CPT], float (&pr)[2][CPT],
-                                       float (&pi)[2][CPT]) {
+// The chains of a thread are processed in pairs with the packed two-lane float
+// instructions of sm_100+ (__ffma2_rn, __fmul2_rn, __fadd2_rn: per component the same
+// IEEE operation as fmaf, *, +), so one instruction advances two chains.  The per-l
+// operands are stored duplicated in shared memory, (A, A, F2, F2), (K0, K0, K1, K1),
+// (w_re, w_re, w_im, w_im), and reach the pair as 64-bit register pairs.
+
+// One l-step of the NP chain pairs: term l into the partial of parity PAR, then the
+// difference-form step to l+1.  kp[p]: the K coefficient of each chain of pair p (K0,
+// or K1 for a mirrored chain).  MASKED: some chain of the warp is still scaled; its term
+// is cur * sp, where sp = 2^(64 n) for the count n of 2^64 factors (1 for a plain chain,
+// 2^-64 for n = -1, 0 below: those terms are < 2^-64 |w|).
+template <int NP, int PAR, bool MASKED>
+__device__ __forceinline__ void step_pairs(const float4 a4, const float2 (&kp)[NP], const float4 w4,
+                                           const float2 (&x2p)[NP], float2 (&cur)[NP], float2 (&aux)[NP],
+                                           const float2 (&sp)[NP], float2 (&pr)[2][NP], float2 (&pi)[2][NP]) {
+    const float2 A = make_float2(a4.x, a4.y), F2 = make_float2(a4.z, a4.w);
+    const float2 WR = make_float2(w4.x, w4.y), WI = make_float2(w4.z, w4.w);
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        const float cm = MASKED ? cur[c] * sp[c] : cur[c];
-        pr[PAR][c] = fmaf(w.x, cm, pr[PAR][c]);
-        pi[PAR][c] = fmaf(w.y, cm, pi[PAR][c]);
-        const int hm = __float_as_int(x2s[c]) >> 31;  // all ones for a mirrored chain
-        const float kk = __int_as_float((__float_as_int(tc.z) & ~hm) | (__float_as_int(tc.w) & hm));
-        const float coef = fmaf(tc.x, fabsf(x2s[c]), kk);
-        aux[c] = fmaf(tc.y, aux[c], coef * cur[c]);
-        cur[c] = cur[c] + aux[c];
+    for (int p = 0; p < NP; ++p) {
+        const float2 cm = MASKED ? __fmul2_rn(cur[p], sp[p]) : cur[p];
+        pr[PAR][p] = __ffma2_rn(WR, cm, pr[PAR][p]);
+        pi[PAR][p] = __ffma2_rn(WI, cm, pi[PAR][p]);
+        const float2 coef = __ffma2_rn(A, x2p[p], kp[p]);
+        aux[p] = __ffma2_rn(F2, aux[p], __fmul2_rn(coef, cur[p]));
+        cur[p] = __fadd2_rn(cur[p], aux[p]);
     }
 }
 
-// Rescaling of the scaled chains, run every RESCALE_EVERY steps of a masked tile: a
+// Rescaling of one scaled chain, run every RESCALE_EVERY steps of a masked tile: a
 // mantissa at or above 2^64 is scaled by 2^-64 (n += 1), one of a scaled chain below
 // 2^-64 by 2^64 (n -= 1), jointly with aux; then sp = 2^(64 n) (0 for n <= -2).  No
 // branch.  Between two calls the mantissa changes by less than 2^60: the ratio of
@@ -210,33 +215,119 @@ __device__ __forceinline__ void step32(const float4 tc, const float2 w, const fl
 // l = l0 + k (largest for m_b = m_sky = l0), so four steps from l0 <= 32767 grow it by
 // at most 2^64 / 24, and a mantissa left in [2^-64, 2^64) stays a normal float.
 constexpr int RESCALE_EVERY = 4;
-template <int CPT>
-__device__ __forceinline__ void rescale32(float (&cur)[CPT], float (&aux)[CPT], int (&nsc)[CPT], float (&sp)[CPT]) {
+__device__ __forceinline__ void rescale32(float &cur, float &aux, int &n, float &sp) {
+    const float m = fabsf(cur);
+    const bool dn = m >= 0x1p64f;
+    const bool up = (m < 0x1p-64f) && (n != 0);
+    const float f = dn ? 0x1p-64f : (up ? 0x1p64f : 1.0f);
+    cur *= f;
+    aux *= f;
+    n += (int)dn - (int)up;
+    sp = __int_as_float(max(0, 127 + 64 * n) << 23);
+}
+
+template <int NP>
+__device__ __forceinline__ void rescale_pairs(float2 (&cur)[NP], float2 (&aux)[NP], int (&nsc)[2 * NP],
+                                              float2 (&sp)[NP]) {
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-        const float m = fabsf(cur[c]);
-        const bool dn = m >= 0x1p64f;
-        const bool up = (m < 0x1p-64f) && (nsc[c] != 0);
-        const float f = dn ? 0x1p-64f : (up ? 0x1p64f : 1.0f);
-        cur[c] *= f;
-        aux[c] *= f;
-        nsc[c] += (int)dn - (int)up;
-        sp[c] = __int_as_float(max(0, 127 + 64 * nsc[c]) << 23);
+    for (int p = 0; p < NP; ++p) {
+        rescale32(cur[p].x, aux[p].x, nsc[2 * p], sp[p].x);
+        rescale32(cur[p].y, aux[p].y, nsc[2 * p + 1], sp[p].y);
     }
 }
 
-// Shared memory of one FP32-form CTA: the l-tile's coefficients and weights, and the
-// per-chain state that is touched once per column or per tile (kept out of registers
-// so that more warps fit on an SM): the seeds' half-angle logarithms and flags, and
-// the Neumaier-compensated sums.
+// Shared memory of one FP32-form CTA: two buffers of the l-tile's operands (the tile
+// after the current one is built while other warps still step the current one), and
+// the per-chain state that is touched once per column or per tile (kept out of
+// registers so that more warps fit on an SM): the seeds' half-angle logarithms and
+// flags, and the Neumaier-compensated sums.
 template <int NT, int CPT, int TL>
 struct SmemFp32 {
-    float4 sT[TL];          // (A = -2 F0, F2, K0, K1) per l
-    float2 sW[TL];          // (w_re, w_im) per l
+    float4 sA[2][TL];       // (A, A, F2, F2), A = -2 F0
+    float4 sK[2][TL];       // (K0, K0, K1, K1)
+    float4 sW[2][TL];       // (w_re, w_re, w_im, w_im)
     float4 sLog[CPT][NT];   // (ln cos(b/2) hi, lo, ln sin(b/2) hi, lo)
     int sFlag[CPT][NT];     // bit 0: bad angle, 1: mirrored, 2: cos(b/2) = 0, 3: sin(b/2) = 0
     float4 sAcc[CPT][NT];   // compensated sums (re, re carry, im, im carry)
 };
+
+// operands of order l (< L + 1) of column (mb, ms) into buffer entry i
+template <int NT, int CPT, int TL>
+__device__ __forceinline__ void build_tile_entry(const ConvArgs &A, const Tables &T, int l, int mb, int ms,
+                                                 float4 &sa, float4 &sk, float4 &sw) {
+    const int MB1 = A.mb_max + 1;
+    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
+    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+    const float ar = d2f_trunc(av.x), ai = d2f_trunc(av.y);
+    const float br = d2f_trunc(bv.x), bi = d2f_trunc(bv.y);
+    const float wr = __fmaf_rn(br, ar, bi * ai), wi = __fmaf_rn(br, ai, -(bi * ar));
+    const float4 c = diff_coefficients(l, A.l_max, mb, ms, T);
+    sa = make_float4(c.x, c.x, c.y, c.y);
+    sk = make_float4(c.z, c.z, c.w, c.w);
+    sw = make_float4(wr, wr, wi, wi);
+}
+
+// the K pair of each chain pair at tile entry i: the thread's common K (UNIFORM: all its
+// chains on the same side of pi/2) or each chain's own (hoff = 2 for a mirrored chain)
+template <int NP, bool UNIFORM>
+__device__ __forceinline__ void k_pairs(const float4 &k4, int thigh, const int (&hoff)[2 * NP], float2 (&kp)[NP]) {
+    if (UNIFORM) {
+        const float2 k = reinterpret_cast<const float2 *>(&k4)[thigh];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) kp[p] = k;
+    } else {
+        const float *kq = reinterpret_cast<const float *>(&k4);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) kp[p] = make_float2(kq[hoff[2 * p]], kq[hoff[2 * p + 1]]);
+    }
+}
+
+// The steps of one l-tile (nl orders) for every chain of the thread.
+template <int NP, int TL, bool UNIFORM>
+__device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, const float4 *sW, int nl, bool plain,
+                                           int thigh, const int (&hoff)[2 * NP], const float2 (&x2p)[NP],
+                                           float2 (&cur)[NP], float2 (&aux)[NP], int (&nsc)[2 * NP],
+                                           float2 (&sp)[NP], float2 (&pr)[2][NP], float2 (&pi)[2][NP]) {
+    float2 kp[NP];
+    int i = 0;
+    if (plain) {  // every chain of the warp is a plain float
+        for (; i + 1 < nl; i += 2) {
+            k_pairs<NP, UNIFORM>(sK[i], thigh, hoff, kp);
+            step_pairs<NP, 0, false>(sA[i], kp, sW[i], x2p, cur, aux, sp, pr, pi);
+            k_pairs<NP, UNIFORM>(sK[i + 1], thigh, hoff, kp);
+            step_pairs<NP, 1, false>(sA[i + 1], kp, sW[i + 1], x2p, cur, aux, sp, pr, pi);
+        }
+        if (i < nl) {
+            k_pairs<NP, UNIFORM>(sK[i], thigh, hoff, kp);
+            step_pairs<NP, 0, false>(sA[i], kp, sW[i], x2p, cur, aux, sp, pr, pi);
+        }
+    } else {
+        static_assert(RESCALE_EVERY == 4, "the masked loop below is unrolled by four");
+        for (; i + 3 < nl; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; q += 2) {
+                k_pairs<NP, UNIFORM>(sK[i + q], thigh, hoff, kp);
+                step_pairs<NP, 0, true>(sA[i + q], kp, sW[i + q], x2p, cur, aux, sp, pr, pi);
+                k_pairs<NP, UNIFORM>(sK[i + q + 1], thigh, hoff, kp);
+                step_pairs<NP, 1, true>(sA[i + q + 1], kp, sW[i + q + 1], x2p, cur, aux, sp, pr, pi);
+            }
+            rescale_pairs(cur, aux, nsc, sp);
+        }
+        if (i < nl) {
+            k_pairs<NP, UNIFORM>(sK[i], thigh, hoff, kp);
+            step_pairs<NP, 0, true>(sA[i], kp, sW[i], x2p, cur, aux, sp, pr, pi);
+            if (i + 1 < nl) {
+                k_pairs<NP, UNIFORM>(sK[i + 1], thigh, hoff, kp);
+                step_pairs<NP, 1, true>(sA[i + 1], kp, sW[i + 1], x2p, cur, aux, sp, pr, pi);
+            }
+            if (i + 2 < nl) {
+                k_pairs<NP, UNIFORM>(sK[i + 2], thigh, hoff, kp);
+                step_pairs<NP, 0, true>(sA[i + 2], kp, sW[i + 2], x2p, cur, aux, sp, pr, pi);
+            }
+            rescale_pairs(cur, aux, nsc, sp);
+        }
+    }
+}
 
 // One work item of the FP32 form: chain columns k in [k_begin, k_end) (m_sky-major
 // order) for the angle chunk `chunk` (NT*CPT angles).  Every thread of the CTA calls it.
@@ -245,30 +336,39 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                                                 int k_end, SmemFp32<NT, CPT, TL> &sm, unsigned long long &n_elem,
                                                 unsigned long long &n_sum) {
     static_assert(TL % 4 == 0, "tile length must be a multiple of 4 (parity of l and the rescale period)");
+    static_assert(CPT % 2 == 0, "chains are processed in pairs");
+    constexpr int NP = CPT / 2;
     const int MB1 = A.mb_max + 1;
     const int L = A.l_max;
     const int NB = A.n_beta;
     const int tid = threadIdx.x;
     const int j0 = chunk * NT * CPT + tid;  // angle of chain c: j0 + c * NT
-    float4 *sT = sm.sT;
-    float2 *sW = sm.sW;
 
-    float x2s[CPT];  // x^2 with the sign bit set for a mirrored chain
+    float2 x2p[NP];   // x^2 of the difference form (sin^2 or, mirrored, cos^2 of beta/2)
+    int hoff[CPT];    // 2 for a mirrored chain (index of K1 in (K0, K0, K1, K1)), else 0
+    bool same = true;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
         const bool valid = j0 + c * NT < NB;
         const Angle32 t = make_angle32(valid ? A.beta[j0 + c * NT] : 1.0);
         if (valid && t.bad) raise_status(T.status, WG_DEVERR_BETA);
-        x2s[c] = t.high ? -t.x2 : t.x2;
+        if (c & 1)
+            x2p[c / 2].y = t.x2;
+        else
+            x2p[c / 2].x = t.x2;
+        hoff[c] = t.high ? 2 : 0;
+        same = same && (hoff[c] == hoff[0]);
         sm.sLog[c][tid] = make_float4(t.lnc.hi, t.lnc.lo, t.lns.hi, t.lns.lo);
         sm.sFlag[c][tid] = (t.bad ? 1 : 0) | (t.high ? 2 : 0) | (t.c_zero ? 4 : 0) | (t.s_zero ? 8 : 0);
     }
+    const int thigh = hoff[0] >> 1;                        // the thread's side when `same`
+    const bool uniform = __all_sync(0xffffffffu, same);    // warp-uniform code path
 
     for (int k = k_begin; k < k_end; ++k) {
         const int ms = k / MB1, mb = k - ms * MB1;
         const int l0 = mb > ms ? mb : ms;
 
-        float cur[CPT], aux[CPT], sp[CPT], pr[2][CPT], pi[2][CPT];
+        float2 cur[NP], aux[NP], sp[NP], pr[2][NP], pi[2][NP];
         int nsc[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
@@ -280,35 +380,35 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             t.c_zero = (fl & 4) != 0;
             t.s_zero = (fl & 8) != 0;
             const Seed32 s = seed32(mb, ms, t, T);
-            // mirrored chains start from e^{l0} = (-1)^{l0} d^{l0}
-            cur[c] = ((fl & 2) && (l0 & 1)) ? -s.mant : s.mant;
-            aux[c] = cur[c];  // Delta_{l0} = d^{l0} - d^{l0-1} = d^{l0}
+            // mirrored chains start from e^{l0} = (-1)^{l0} d^{l0}; Delta_{l0} = d^{l0}
+            const float v = ((fl & 2) && (l0 & 1)) ? -s.mant : s.mant;
+            const float spv = (s.n == 0) ? 1.0f : 0.0f;  // a scaled seed has n <= -2
+            if (c & 1) {
+                cur[c / 2].y = v;
+                aux[c / 2].y = v;
+                sp[c / 2].y = spv;
+            } else {
+                cur[c / 2].x = v;
+                aux[c / 2].x = v;
+                sp[c / 2].x = spv;
+            }
             nsc[c] = s.n;
-            sp[c] = (s.n == 0) ? 1.0f : 0.0f;  // a scaled seed has n <= -2
             if (s.n == 0 && j0 + c * NT < NB) n_sum += (unsigned long long)(L + 1 - l0);
             sm.sAcc[c][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         bool warp_plain = false;
 
-        for (int ts = l0; ts <= L; ts += TL) {
-            __syncthreads();
-            for (int i = tid; i < TL; i += NT) {
-                const int l = ts + i;
-                float2 w = make_float2(0.f, 0.f);
-                if (l <= L) {
-                    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
-                    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
-                    const float ar = d2f_trunc(av.x), ai = d2f_trunc(av.y);
-                    const float br = d2f_trunc(bv.x), bi = d2f_trunc(bv.y);
-                    w = make_float2(__fmaf_rn(br, ar, bi * ai), __fmaf_rn(br, ai, -(bi * ar)));
-                }
-                sT[i] = (l <= L) ? diff_coefficients(l, L, mb, ms, T) : make_float4(0.f, 0.f, 0.f, 0.f);
-                sW[i] = w;
-            }
-            __syncthreads();
+        // first tile's operands into buffer 0
+        __syncthreads();  // the previous column's readers of both buffers are done
+        for (int i = tid; i < TL; i += NT)
+            if (l0 + i <= L) build_tile_entry<NT, CPT, TL>(A, T, l0 + i, mb, ms, sm.sA[0][i], sm.sK[0][i], sm.sW[0][i]);
+        __syncthreads();
+
+        int buf = 0;
+        for (int ts = l0; ts <= L; ts += TL, buf ^= 1) {
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                pr[0][c] = pr[1][c] = pi[0][c] = pi[1][c] = 0.f;
+            for (int p = 0; p < NP; ++p) {
+                pr[0][p] = pr[1][p] = pi[0][p] = pi[1][p] = make_float2(0.f, 0.f);
             }
             const int nl = min(TL, L + 1 - ts);
             if (!warp_plain) {
@@ -318,50 +418,47 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) {
                     if (nsc[c] == -1) {
-                        cur[c] *= 0x1p-64f;
-                        aux[c] *= 0x1p-64f;
+                        float &cu = (c & 1) ? cur[c / 2].y : cur[c / 2].x;
+                        float &au = (c & 1) ? aux[c / 2].y : aux[c / 2].x;
+                        float &su = (c & 1) ? sp[c / 2].y : sp[c / 2].x;
+                        cu *= 0x1p-64f;
+                        au *= 0x1p-64f;
+                        su = 1.0f;
                         nsc[c] = 0;
-                        sp[c] = 1.0f;
                         if (j0 + c * NT < NB) n_sum += (unsigned long long)(L + 1 - ts);
                     }
                     p = p && (nsc[c] == 0);
                 }
                 warp_plain = __all_sync(0xffffffffu, p);
             }
-            int i = 0;
-            if (warp_plain) {  // every chain of the warp is a plain float from here on
-                for (; i + 1 < nl; i += 2) {
-                    step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
-                    step32<CPT, 1, false>(sT[i + 1], sW[i + 1], x2s, cur, aux, sp, pr, pi);
-                }
-                if (i < nl) step32<CPT, 0, false>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
-            } else {
-                static_assert(RESCALE_EVERY == 4, "the masked loop below is unrolled by four");
-                for (; i + 3 < nl; i += 4) {
-                    step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
-                    step32<CPT, 1, true>(sT[i + 1], sW[i + 1], x2s, cur, aux, sp, pr, pi);
-                    step32<CPT, 0, true>(sT[i + 2], sW[i + 2], x2s, cur, aux, sp, pr, pi);
-                    step32<CPT, 1, true>(sT[i + 3], sW[i + 3], x2s, cur, aux, sp, pr, pi);
-                    rescale32(cur, aux, nsc, sp);
-                }
-                if (i < nl) {
-                    step32<CPT, 0, true>(sT[i], sW[i], x2s, cur, aux, sp, pr, pi);
-                    if (i + 1 < nl) step32<CPT, 1, true>(sT[i + 1], sW[i + 1], x2s, cur, aux, sp, pr, pi);
-                    if (i + 2 < nl) step32<CPT, 0, true>(sT[i + 2], sW[i + 2], x2s, cur, aux, sp, pr, pi);
-                    rescale32(cur, aux, nsc, sp);
-                }
-            }
+            if (uniform)
+                tile_steps<NP, TL, true>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hoff, x2p, cur,
+                                         aux, nsc, sp, pr, pi);
+            else
+                tile_steps<NP, TL, false>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hoff, x2p, cur,
+                                          aux, nsc, sp, pr, pi);
+            // the next tile's operands into the other buffer (its previous readers passed
+            // the barrier at the end of the last tile), then one barrier
+            for (int i = tid; i < TL; i += NT)
+                if (ts + TL + i <= L)
+                    build_tile_entry<NT, CPT, TL>(A, T, ts + TL + i, mb, ms, sm.sA[buf ^ 1][i], sm.sK[buf ^ 1][i],
+                                                  sm.sW[buf ^ 1][i]);
             // partials of this tile into the compensated sums; the sign of the odd-offset
             // partial is (-1) for mirrored chains, and the tile's start parity (that of
             // l0, as TL is even) is applied at the end
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
-                const float sg = (__float_as_int(x2s[c]) < 0) ? -1.f : 1.f;
+                const float sg = hoff[c] ? -1.f : 1.f;
+                const float p0r = (c & 1) ? pr[0][c / 2].y : pr[0][c / 2].x;
+                const float p1r = (c & 1) ? pr[1][c / 2].y : pr[1][c / 2].x;
+                const float p0i = (c & 1) ? pi[0][c / 2].y : pi[0][c / 2].x;
+                const float p1i = (c & 1) ? pi[1][c / 2].y : pi[1][c / 2].x;
                 float4 acc = sm.sAcc[c][tid];
-                neumaier_add(acc.x, acc.y, pr[0][c] + sg * pr[1][c]);
-                neumaier_add(acc.z, acc.w, pi[0][c] + sg * pi[1][c]);
+                neumaier_add(acc.x, acc.y, p0r + sg * p1r);
+                neumaier_add(acc.z, acc.w, p0i + sg * p1i);
                 sm.sAcc[c][tid] = acc;
             }
+            __syncthreads();
         }
         double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
 #pragma unroll

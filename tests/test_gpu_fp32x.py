@@ -72,6 +72,23 @@ def test_conv_fp32x_small(W, L, MB, MS, NB):
     assert np.all(np.isfinite(C))
 
 
+def test_conv_fp32x_unsorted_angles_with_poles(W):
+    """Angles in random order, both poles and pi/2 included: threads hold chains on both
+    sides of pi/2 (each chain picks its own K coefficient) and scaled and plain chains
+    share warps; also two angle chunks of 512."""
+    L, MB, MS, NB = 900, 6, 900, 700
+    beta = np.concatenate([[0.0, 1e-4, math.pi / 2, math.pi - 1e-4, math.pi],
+                           I.beta_uniform(NB - 5, 1e-3, math.pi - 1e-3, 9)])
+    np.random.default_rng(10).shuffle(beta)
+    a = I.sky_alm(L, MS, 11)
+    b = I.beam_blm(L, MB, fwhm=0.02)
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form="fp32x").cpu().numpy()
+    W.check_device_status()
+    ref = O.conv_sum(L, MB, MS, beta, a, b)
+    assert _rel_l2(C, ref) <= 1e-4
+    assert np.all(np.isfinite(C))
+
+
 def test_conv_fp32x_l8192(W):
     """Full 8192/16/8192 sum on 8192 GL angles; vs the FP64 kernel (every 16th angle) and the oracle."""
     L, MB, MS, beta, a, b = I.make_config("conv_fp32x_l8192")
