@@ -290,6 +290,9 @@ def run_ours(args):
     grad = None
     if not args.skip_grad:
         grad = _grad_block(W, dev, stream, args)
+    dtable = None
+    if not args.skip_dtable:
+        dtable = _dtable_block(W, dev, stream, args)
 
     if rank != 0:
         if dist is not None:
@@ -328,7 +331,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "conv_fp64_kernel",
+                     "kernel": FP64_KERNEL,
                      "flops_per_launch": flops_launch, "summed_elements": n_sum, "elements": n_elem,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                      "fma_microbench_tflops": peak_meas},
@@ -336,6 +339,7 @@ def run_ours(args):
         "fp64s": fp64s,
         "fp32x": fp32x,
         "grad": grad,
+        "dtable": dtable,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -411,6 +415,55 @@ def _grad_block(W, dev, stream, args):
     return {"workload": "grad_l2048 (L=2048, m_b<=8, m_sky<=2048, 1024 uniform angles)",
             "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
             "forward_evals_per_s": elems / (ms_f / 1e3), "backward_evals_per_s": elems / (ms_b / 1e3)}
+
+
+def _hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (driver-written), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def _dtable_block(W, dev, stream, args):
+    """The full d-table workload (L=256, m_b<=4, m_sky<=256, 64 equispaced angles; the
+    table, zeros for l < l0 included, is 169 MB of float64): time per launch of both
+    forms, evaluations per second and the HBM write rate against the measured copy
+    bandwidth.  A buffer larger than L2 is written between timed launches."""
+    import torch
+    from paper_1002_1050_gb300 import inputs as I
+
+    L, MB, MS, beta_h, _, _ = I.make_config("dtable_l256")
+    beta = torch.from_numpy(beta_h).to(dev)
+    out = torch.empty((MB + 1, MS + 1, L + 1, beta.numel()), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > L2
+    elems = I.n_elements(L, MB, MS, beta.numel())
+    nbytes = out.numel() * 8
+    peak, peak_src = _hbm_peak_gbs()
+    res = {"workload": "dtable_l256 (L=256, m_b<=4, m_sky<=256, 64 equispaced angles)", "elements": elems,
+           "bytes_written": nbytes, "l2": "a 256 MB buffer is written between timed launches"}
+    for form in ("fp64", "fp32x"):
+        W.wigner_d_table(beta, L, MB, MS, form=form, out=out)
+        torch.cuda.synchronize()
+        W.check_device_status()
+        times = []
+        for _ in range(args.dtable_steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            W.wigner_d_table(beta, L, MB, MS, form=form, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        gbs = nbytes / (ms / 1e3) / 1e9
+        res[form] = {"us_per_launch": 1e3 * ms, "evals_per_s": elems / (ms / 1e3),
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": gbs / peak, "peak_source": peak_src}}
+    del out, flush
+    torch.cuda.empty_cache()
+    return res
 
 
 def _fp32x_block(W, dev, stream, args):
@@ -532,12 +585,19 @@ def run_batched(args):
     return 0
 
 
+# the dominant kernel as launched by wigner_conv_sum(form="fp64"); the committed DRAM
+# counters count only if they were taken on this same kernel
+FP64_KERNEL = "conv_fp64_kernel<256,2,128,false>"
+
+
 def _profile_traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if current."""
     path = os.path.join(ROOT, "profiles", "conv_fp64_l4096_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
+        if d.get("kernel") != FP64_KERNEL:
+            return None
         return d.get("bytes_per_launch")
     except Exception:
         return None
@@ -547,7 +607,8 @@ def main(argv=None):
     global N_BETA
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default 10; 2 for --workload batched, whose step takes ~30 s)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["conv_fp64_l4096", "batched"], default="conv_fp64_l4096",
@@ -559,6 +620,8 @@ def main(argv=None):
     p.add_argument("--skip-fp32x", action="store_true", help="skip the FP32-form measurement")
     p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
     p.add_argument("--skip-grad", action="store_true", help="skip the forward/adjoint timing")
+    p.add_argument("--skip-dtable", action="store_true", help="skip the d-table timing")
+    p.add_argument("--dtable-steps", type=int, default=20)
     p.add_argument("--fp64s-steps", type=int, default=5)
     p.add_argument("--fp32x-steps", type=int, default=3)
     p.add_argument("--fp32x-n-beta", type=int, default=8192,
@@ -569,6 +632,8 @@ def main(argv=None):
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     N_BETA = args.n_beta
+    if args.steps is None:
+        args.steps = 2 if args.workload == "batched" else 10
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

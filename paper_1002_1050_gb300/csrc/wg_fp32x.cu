@@ -7,7 +7,7 @@
 namespace wg {
 
 template <int NT, int CPT, int TL>
-__global__ void __launch_bounds__(NT) conv_fp32x_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
+__global__ void __launch_bounds__(NT, 6) conv_fp32x_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
     __shared__ SmemFp32<NT, CPT, TL> sm;
     const int item = blockIdx.x;
     const int chunk = item % n_chunks;
@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(NT) dtable_fp32x_kernel(DTableArgs A, Tables T
         __syncthreads();
         for (int i = threadIdx.x; i < TL; i += NT) {
             const int l = ts + i;
-            sT[i] = (l <= L) ? diff_coefficients(l, L, mb, ms, T) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 raw;
+            sT[i] = (l <= L) ? diff_coefficients(l, L, mb, ms, T, raw) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
         const int nl = min(TL, L + 1 - ts);

@@ -56,6 +56,8 @@ struct Angle32 {
     bool bad;     // beta outside [0, pi] or NaN
     bool c_zero, s_zero;
     ff lnc, lns;  // ln cos(beta/2), ln sin(beta/2)
+    float cb;     // cos(beta)
+    float sb;     // sin(beta)
 };
 
 __device__ __forceinline__ ff dbl_ff(double x) {
@@ -75,6 +77,8 @@ __device__ __forceinline__ Angle32 make_angle32(double beta) {
     t.c_zero = (c <= 0.0);
     t.lnc = dbl_ff((c >= s) ? 0.5 * log1p(-s * s) : log(c));
     t.lns = dbl_ff((s >= c) ? 0.5 * log1p(-c * c) : log(s));
+    t.cb = __double2float_rn((c - s) * (c + s));
+    t.sb = __double2float_rn(2.0 * s * c);
     return t;
 }
 
@@ -157,8 +161,11 @@ struct Tile32 {
 // float-float on the FP32 pipe from the float-float tables and rounded to float:
 // K0 = F0 (1 - F1) - 1 - F2 and K1 = F0 (1 + F1) - 1 - F2 are small where the form
 // matters and keep their relative precision because the cancellation happens in ff.
-__device__ __forceinline__ float4 diff_coefficients(int l, int L, int mb, int ms, const Tables &T) {
-    if (l >= L) return make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ float4 diff_coefficients(int l, int L, int mb, int ms, const Tables &T, float4 &raw) {
+    if (l >= L) {
+        raw = make_float4(0.f, 0.f, 1.f, 0.f);
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const ff pp = ff_mul(ff_mul(ff_of(T.P_f[l + mb]), ff_of(T.P_f[l - mb])),
                          ff_mul(ff_of(T.P_f[l + ms]), ff_of(T.P_f[l - ms])));
     const ff qq = ff_mul(ff_mul(ff_of(T.Q_f[l + mb]), ff_of(T.Q_f[l - mb])),
@@ -169,6 +176,7 @@ __device__ __forceinline__ float4 diff_coefficients(int l, int L, int mb, int ms
     const ff base = ff_add(ff_add(f0, ff{-1.0f, 0.0f}), ff_neg(f2));
     const ff k0 = ff_add(base, ff_neg(g));
     const ff k1 = ff_add(base, g);
+    raw = make_float4(f0.hi, g.hi, f2.hi, f2.lo);  // F0, G = F0 F1, F2 (float-float)
     return make_float4(-2.0f * f0.hi, f2.hi, __fadd_rn(k0.hi, k0.lo), __fadd_rn(k1.hi, k1.lo));
 }
 
@@ -236,35 +244,135 @@ __device__ __forceinline__ void rescale_pairs(float2 (&cur)[NP], float2 (&aux)[N
     }
 }
 
-// Shared memory of one FP32-form CTA: two buffers of the l-tile's operands (the tile
-// after the current one is built while other warps still step the current one), and
-// the per-chain state that is touched once per column or per tile (kept out of
-// registers so that more warps fit on an SM): the seeds' half-angle logarithms and
-// flags, and the Neumaier-compensated sums.
+// One l-step of the NP chain pairs in the normalised form (bulk angles): the chain is
+// carried as u^l = d^l / sigma_l (sigma_{l0} = sigma_{l0+1} = 1, sigma_{l+1} =
+// F2_l sigma_{l-1}), so Eq. lrec reads u^{l+1} = (F0'_l cos b - G'_l) u^l - u^{l-1}
+// with F0' = F0 rho_l, G' = G rho_l, rho_l = sigma_l / sigma_{l+1}: two packed
+// instructions per pair for the recursion, two for the sum of (w_l sigma_l) u^l.
+// n4 = (F0', F0', -G', -G'), w4 = (w sigma)(re, re, im, im).
+template <int NP, int PAR, bool MASKED>
+__device__ __forceinline__ void step_norm(const float4 n4, const float4 w4, const float2 (&cbp)[NP],
+                                          float2 (&u)[NP], float2 (&up)[NP], const float2 (&sp)[NP],
+                                          float2 (&pr)[2][NP], float2 (&pi)[2][NP]) {
+    const float2 F = make_float2(n4.x, n4.y), NG = make_float2(n4.z, n4.w);
+    const float2 WR = make_float2(w4.x, w4.y), WI = make_float2(w4.z, w4.w);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float2 cm = MASKED ? __fmul2_rn(u[p], sp[p]) : u[p];
+        pr[PAR][p] = __ffma2_rn(WR, cm, pr[PAR][p]);
+        pi[PAR][p] = __ffma2_rn(WI, cm, pi[PAR][p]);
+        const float2 y = __ffma2_rn(F, cbp[p], NG);
+        const float2 nx = __ffma2_rn(y, u[p], make_float2(-up[p].x, -up[p].y));
+        up[p] = u[p];
+        u[p] = nx;
+    }
+}
+
+// Shared memory of one FP32-form CTA: two buffers of the difference form's l-tile
+// operands (the tile after the current one is built while other warps still step the
+// current one), one of the normalised form's (built from the raw coefficients after a
+// barrier), and the per-chain state that is touched once per column or per tile (kept
+// out of registers so that more warps fit on an SM): the seeds' half-angle
+// logarithms and flags, and the Neumaier-compensated sums.
 template <int NT, int CPT, int TL>
 struct SmemFp32 {
     float4 sA[2][TL];       // (A, A, F2, F2), A = -2 F0
     float4 sK[2][TL];       // (K0, K0, K1, K1)
     float4 sW[2][TL];       // (w_re, w_re, w_im, w_im)
+    float4 sRaw[TL];        // (F0, G, F2 hi, F2 lo) of the tile being built
+    float4 sN[TL];          // (F0', F0', -G', -G') of the normalised form
+    float4 sWn[TL];         // (w sigma)(re, re, im, im)
+    float4 sSig;            // sigma at the entries -1 and 0 of the next tile (float-float)
     float4 sLog[CPT][NT];   // (ln cos(b/2) hi, lo, ln sin(b/2) hi, lo)
     int sFlag[CPT][NT];     // bit 0: bad angle, 1: mirrored, 2: cos(b/2) = 0, 3: sin(b/2) = 0
     float4 sAcc[CPT][NT];   // compensated sums (re, re carry, im, im carry)
 };
 
-// operands of order l (< L + 1) of column (mb, ms) into buffer entry i
+// operands of order l (<= L) of column (mb, ms) into tile entry i of buffer buf; F2 of
+// the first order l0 is entered as 1 (sigma_{l0+1} = sigma_{l0}), as is F2 past l_max
 template <int NT, int CPT, int TL>
-__device__ __forceinline__ void build_tile_entry(const ConvArgs &A, const Tables &T, int l, int mb, int ms,
-                                                 float4 &sa, float4 &sk, float4 &sw) {
+__device__ __forceinline__ void build_tile_entry(const ConvArgs &A, const Tables &T, int l, int l0, int mb, int ms,
+                                                 SmemFp32<NT, CPT, TL> &sm, int buf, int i) {
     const int MB1 = A.mb_max + 1;
     const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
     const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
     const float ar = d2f_trunc(av.x), ai = d2f_trunc(av.y);
     const float br = d2f_trunc(bv.x), bi = d2f_trunc(bv.y);
     const float wr = __fmaf_rn(br, ar, bi * ai), wi = __fmaf_rn(br, ai, -(bi * ar));
-    const float4 c = diff_coefficients(l, A.l_max, mb, ms, T);
-    sa = make_float4(c.x, c.x, c.y, c.y);
-    sk = make_float4(c.z, c.z, c.w, c.w);
-    sw = make_float4(wr, wr, wi, wi);
+    float4 raw;
+    const float4 c = diff_coefficients(l, A.l_max, mb, ms, T, raw);
+    if (l == l0) {
+        raw.z = 1.0f;
+        raw.w = 0.0f;
+    }
+    sm.sA[buf][i] = make_float4(c.x, c.x, c.y, c.y);
+    sm.sK[buf][i] = make_float4(c.z, c.z, c.w, c.w);
+    sm.sW[buf][i] = make_float4(wr, wr, wi, wi);
+    sm.sRaw[i] = raw;
+}
+
+// The normalised form's operands of a built tile, by one warp: sigma over the tile by
+// a float-float product scan of F2 along each parity of l, sigma_{e+1} = F2_e
+// sigma_{e-1} (carry in sSig: sigma at the entries -1 and 0, replaced by the next
+// tile's), then rho = sigma_e / sigma_{e+1}, F0' = F0 rho, G' = G rho, w sigma.  Lane t
+// owns entries EPL t .. EPL t + EPL - 1.
+template <int NT, int CPT, int TL>
+__device__ __forceinline__ void normalise_tile(SmemFp32<NT, CPT, TL> &sm, int buf, int nl, int lane) {
+    constexpr int EPL = TL / 32;
+    static_assert(TL % 64 == 0, "an even number of entries per lane");
+    const int e0 = EPL * lane;
+    // products of the lane's factors on each parity chain
+    ff pe{1.0f, 0.0f}, po{1.0f, 0.0f};  // factors of odd entries (even chain), of even entries (odd chain)
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+        const float4 r = sm.sRaw[e0 + q];
+        const ff f = (e0 + q < nl) ? ff{r.z, r.w} : ff{1.0f, 0.0f};
+        if (q & 1)
+            pe = ff_mul(pe, f);
+        else
+            po = ff_mul(po, f);
+    }
+    // inclusive product scans over the lanes, then exclusive
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const ff e{__shfl_up_sync(0xffffffffu, pe.hi, off), __shfl_up_sync(0xffffffffu, pe.lo, off)};
+        const ff o{__shfl_up_sync(0xffffffffu, po.hi, off), __shfl_up_sync(0xffffffffu, po.lo, off)};
+        if (lane >= off) {
+            pe = ff_mul(pe, e);
+            po = ff_mul(po, o);
+        }
+    }
+    ff xe{__shfl_up_sync(0xffffffffu, pe.hi, 1), __shfl_up_sync(0xffffffffu, pe.lo, 1)};
+    ff xo{__shfl_up_sync(0xffffffffu, po.hi, 1), __shfl_up_sync(0xffffffffu, po.lo, 1)};
+    if (lane == 0) xe = xo = ff{1.0f, 0.0f};
+    const float4 carry = sm.sSig;
+    ff se = ff_mul(ff{carry.z, carry.w}, xe);  // sigma at the lane's first entry (even)
+    ff so = ff_mul(ff{carry.x, carry.y}, xo);  // sigma at the entry before it (odd)
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+        const int e = e0 + q;
+        const float4 r = sm.sRaw[e];
+        const ff f = (e < nl) ? ff{r.z, r.w} : ff{1.0f, 0.0f};
+        float s_e, s_n;  // sigma_e, sigma_{e+1}
+        if (q & 1) {
+            s_e = so.hi;
+            se = ff_mul(se, f);
+            s_n = se.hi;
+        } else {
+            s_e = se.hi;
+            so = ff_mul(so, f);
+            s_n = so.hi;
+        }
+        const float4 w = sm.sW[buf][e];
+        const float rho = __fdiv_rn(s_e, s_n);
+        const float f0p = r.x * rho, gp = r.y * rho;
+        const float wr = w.x * s_e, wi = w.z * s_e;
+        sm.sN[e] = (e < nl) ? make_float4(f0p, f0p, -gp, -gp) : make_float4(0.f, 0.f, 0.f, 0.f);
+        sm.sWn[e] = (e < nl) ? make_float4(wr, wr, wi, wi) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // carry: sigma at the tile's last two entries (lane 31: so = sigma_{TL-1}, se = sigma_{TL})
+    __syncwarp();
+    if (lane == 31) sm.sSig = make_float4(so.hi, so.lo, se.hi, se.lo);
 }
 
 // the K pair of each chain pair at tile entry i: the thread's common K (UNIFORM: all its
@@ -282,7 +390,7 @@ __device__ __forceinline__ void k_pairs(const float4 &k4, int thigh, const int (
     }
 }
 
-// The steps of one l-tile (nl orders) for every chain of the thread.
+// The steps of one l-tile (nl orders) in the difference form for every chain of the thread.
 template <int NP, int TL, bool UNIFORM>
 __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, const float4 *sW, int nl, bool plain,
                                            int thigh, const int (&hoff)[2 * NP], const float2 (&x2p)[NP],
@@ -329,6 +437,45 @@ __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, c
     }
 }
 
+// The steps of one l-tile in the normalised form ((cur, aux) hold (u^l, u^{l-1})).
+template <int NP, int TL>
+__device__ __forceinline__ void tile_steps_norm(const float4 *sN, const float4 *sWn, int nl, bool plain,
+                                                const float2 (&cbp)[NP], float2 (&cur)[NP], float2 (&aux)[NP],
+                                                int (&nsc)[2 * NP], float2 (&sp)[NP], float2 (&pr)[2][NP],
+                                                float2 (&pi)[2][NP]) {
+    int i = 0;
+    if (plain) {
+        for (; i + 1 < nl; i += 2) {
+            step_norm<NP, 0, false>(sN[i], sWn[i], cbp, cur, aux, sp, pr, pi);
+            step_norm<NP, 1, false>(sN[i + 1], sWn[i + 1], cbp, cur, aux, sp, pr, pi);
+        }
+        if (i < nl) step_norm<NP, 0, false>(sN[i], sWn[i], cbp, cur, aux, sp, pr, pi);
+    } else {
+        for (; i + 3 < nl; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; q += 2) {
+                step_norm<NP, 0, true>(sN[i + q], sWn[i + q], cbp, cur, aux, sp, pr, pi);
+                step_norm<NP, 1, true>(sN[i + q + 1], sWn[i + q + 1], cbp, cur, aux, sp, pr, pi);
+            }
+            rescale_pairs(cur, aux, nsc, sp);
+        }
+        if (i < nl) {
+            step_norm<NP, 0, true>(sN[i], sWn[i], cbp, cur, aux, sp, pr, pi);
+            if (i + 1 < nl) step_norm<NP, 1, true>(sN[i + 1], sWn[i + 1], cbp, cur, aux, sp, pr, pi);
+            if (i + 2 < nl) step_norm<NP, 0, true>(sN[i + 2], sWn[i + 2], cbp, cur, aux, sp, pr, pi);
+            rescale_pairs(cur, aux, nsc, sp);
+        }
+    }
+}
+
+// Angles where the normalised float recursion is used: sin(beta) >= max(0.1, 1.2e-5 l_max).
+// There its error stays near 3e-5 (emulated against the FP64 oracle: it grows like
+// l / sin(beta)); closer to the poles the difference form runs.  Chains starting at
+// l0 >= 8192 also run the difference form: the growth bound of the four steps between
+// rescales holds for the normalised form (ratio <= 4 F0 + 1 with rho <= 2) only below.
+__device__ __forceinline__ float bulk_sin_threshold(int L) { return fmaxf(0.1f, 1.2e-5f * (float)L); }
+constexpr int NORM_L0_LIMIT = 8192;
+
 // One work item of the FP32 form: chain columns k in [k_begin, k_end) (m_sky-major
 // order) for the angle chunk `chunk` (NT*CPT angles).  Every thread of the CTA calls it.
 template <int NT, int CPT, int TL>
@@ -341,32 +488,41 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
     const int MB1 = A.mb_max + 1;
     const int L = A.l_max;
     const int NB = A.n_beta;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int j0 = chunk * NT * CPT + tid;  // angle of chain c: j0 + c * NT
 
     float2 x2p[NP];   // x^2 of the difference form (sin^2 or, mirrored, cos^2 of beta/2)
+    float2 cbp[NP];   // cos(beta) (normalised form)
     int hoff[CPT];    // 2 for a mirrored chain (index of K1 in (K0, K0, K1, K1)), else 0
-    bool same = true;
+    bool same = true, bulk = true;
+    const float sthr = bulk_sin_threshold(L);
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
         const bool valid = j0 + c * NT < NB;
         const Angle32 t = make_angle32(valid ? A.beta[j0 + c * NT] : 1.0);
         if (valid && t.bad) raise_status(T.status, WG_DEVERR_BETA);
-        if (c & 1)
+        if (c & 1) {
             x2p[c / 2].y = t.x2;
-        else
+            cbp[c / 2].y = t.cb;
+        } else {
             x2p[c / 2].x = t.x2;
+            cbp[c / 2].x = t.cb;
+        }
         hoff[c] = t.high ? 2 : 0;
         same = same && (hoff[c] == hoff[0]);
+        bulk = bulk && (t.sb >= sthr) && !t.bad;
         sm.sLog[c][tid] = make_float4(t.lnc.hi, t.lnc.lo, t.lns.hi, t.lns.lo);
         sm.sFlag[c][tid] = (t.bad ? 1 : 0) | (t.high ? 2 : 0) | (t.c_zero ? 4 : 0) | (t.s_zero ? 8 : 0);
     }
-    const int thigh = hoff[0] >> 1;                        // the thread's side when `same`
-    const bool uniform = __all_sync(0xffffffffu, same);    // warp-uniform code path
+    const int thigh = hoff[0] >> 1;                          // the thread's side when `same`
+    const bool uniform = __all_sync(0xffffffffu, same);      // warp-uniform code paths
+    const bool wbulk = __all_sync(0xffffffffu, bulk);
 
     for (int k = k_begin; k < k_end; ++k) {
         const int ms = k / MB1, mb = k - ms * MB1;
         const int l0 = mb > ms ? mb : ms;
+        const bool norm = wbulk && l0 < NORM_L0_LIMIT;  // this warp runs the normalised form
+        const bool need_norm = __syncthreads_or(norm) != 0;
 
         float2 cur[NP], aux[NP], sp[NP], pr[2][NP], pi[2][NP];
         int nsc[CPT];
@@ -380,16 +536,18 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             t.c_zero = (fl & 4) != 0;
             t.s_zero = (fl & 8) != 0;
             const Seed32 s = seed32(mb, ms, t, T);
-            // mirrored chains start from e^{l0} = (-1)^{l0} d^{l0}; Delta_{l0} = d^{l0}
-            const float v = ((fl & 2) && (l0 & 1)) ? -s.mant : s.mant;
+            // difference form: mirrored chains start from e^{l0} = (-1)^{l0} d^{l0},
+            // Delta_{l0} = d^{l0}; normalised form: u^{l0} = d^{l0}, u^{l0-1} = 0
+            const float v = (!norm && (fl & 2) && (l0 & 1)) ? -s.mant : s.mant;
+            const float av = norm ? 0.0f : v;
             const float spv = (s.n == 0) ? 1.0f : 0.0f;  // a scaled seed has n <= -2
             if (c & 1) {
                 cur[c / 2].y = v;
-                aux[c / 2].y = v;
+                aux[c / 2].y = av;
                 sp[c / 2].y = spv;
             } else {
                 cur[c / 2].x = v;
-                aux[c / 2].x = v;
+                aux[c / 2].x = av;
                 sp[c / 2].x = spv;
             }
             nsc[c] = s.n;
@@ -397,12 +555,16 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             sm.sAcc[c][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         bool warp_plain = false;
+        if (tid == 0) sm.sSig = make_float4(1.0f, 0.0f, 1.0f, 0.0f);  // sigma_{l0-1} (entered as 1), sigma_{l0}
 
         // first tile's operands into buffer 0
-        __syncthreads();  // the previous column's readers of both buffers are done
         for (int i = tid; i < TL; i += NT)
-            if (l0 + i <= L) build_tile_entry<NT, CPT, TL>(A, T, l0 + i, mb, ms, sm.sA[0][i], sm.sK[0][i], sm.sW[0][i]);
+            if (l0 + i <= L) build_tile_entry<NT, CPT, TL>(A, T, l0 + i, l0, mb, ms, sm, 0, i);
         __syncthreads();
+        if (need_norm) {
+            if (tid < 32) normalise_tile<NT, CPT, TL>(sm, 0, min(TL, L + 1 - l0), lane);
+            __syncthreads();
+        }
 
         int buf = 0;
         for (int ts = l0; ts <= L; ts += TL, buf ^= 1) {
@@ -431,24 +593,20 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 }
                 warp_plain = __all_sync(0xffffffffu, p);
             }
-            if (uniform)
+            if (norm)
+                tile_steps_norm<NP, TL>(sm.sN, sm.sWn, nl, warp_plain, cbp, cur, aux, nsc, sp, pr, pi);
+            else if (uniform)
                 tile_steps<NP, TL, true>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hoff, x2p, cur,
                                          aux, nsc, sp, pr, pi);
             else
                 tile_steps<NP, TL, false>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hoff, x2p, cur,
                                           aux, nsc, sp, pr, pi);
-            // the next tile's operands into the other buffer (its previous readers passed
-            // the barrier at the end of the last tile), then one barrier
-            for (int i = tid; i < TL; i += NT)
-                if (ts + TL + i <= L)
-                    build_tile_entry<NT, CPT, TL>(A, T, ts + TL + i, mb, ms, sm.sA[buf ^ 1][i], sm.sK[buf ^ 1][i],
-                                                  sm.sW[buf ^ 1][i]);
             // partials of this tile into the compensated sums; the sign of the odd-offset
-            // partial is (-1) for mirrored chains, and the tile's start parity (that of
-            // l0, as TL is even) is applied at the end
+            // partial is (-1) for mirrored chains of the difference form, and the tile's
+            // start parity (that of l0, as TL is even) is applied at the end
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
-                const float sg = hoff[c] ? -1.f : 1.f;
+                const float sg = (hoff[c] && !norm) ? -1.f : 1.f;
                 const float p0r = (c & 1) ? pr[0][c / 2].y : pr[0][c / 2].x;
                 const float p1r = (c & 1) ? pr[1][c / 2].y : pr[1][c / 2].x;
                 const float p0i = (c & 1) ? pi[0][c / 2].y : pi[0][c / 2].x;
@@ -458,7 +616,19 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 neumaier_add(acc.z, acc.w, p0i + sg * p1i);
                 sm.sAcc[c][tid] = acc;
             }
-            __syncthreads();
+            // the next tile: its operands into the other buffer (their previous readers
+            // passed the barrier at the end of the last tile), a barrier, then the
+            // normalised form's operands (one warp) and a second barrier
+            const int tn = ts + TL;
+            if (tn <= L) {
+                for (int i = tid; i < TL; i += NT)
+                    if (tn + i <= L) build_tile_entry<NT, CPT, TL>(A, T, tn + i, l0, mb, ms, sm, buf ^ 1, i);
+                __syncthreads();
+                if (need_norm) {
+                    if (tid < 32) normalise_tile<NT, CPT, TL>(sm, buf ^ 1, min(TL, L + 1 - tn), lane);
+                    __syncthreads();
+                }
+            }
         }
         double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
 #pragma unroll
@@ -467,7 +637,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             if (j < NB) {
                 const int fl = sm.sFlag[c][tid];
                 const float4 acc = sm.sAcc[c][tid];
-                const double sg = ((fl & 2) && (l0 & 1)) ? -1.0 : 1.0;
+                const double sg = (!norm && (fl & 2) && (l0 & 1)) ? -1.0 : 1.0;
                 const double nan = __longlong_as_double(0x7ff8000000000000LL);
                 const double re = sg * ((double)acc.x + (double)acc.y);
                 const double im = sg * ((double)acc.z + (double)acc.w);
@@ -475,6 +645,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 n_elem += (unsigned long long)(L + 1 - l0);
             }
         }
+        __syncthreads();  // the sums and buffers are reused by the next column
     }
 }
 

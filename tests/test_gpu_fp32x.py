@@ -112,3 +112,32 @@ def test_conv_fp32x_l8192(W):
     got = C32[ti[0], ti[1], ti[2]].cpu().numpy()
     ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
     assert _rel_l2(got, ref) <= 1e-4
+
+
+def test_conv_fp32x_size_limits_sampled(W):
+    """The FP32 form at the longest chains (l_max = 32767) and at chains starting at
+    m_b = m_sky ~ 2000 (the fastest growth in the four steps between rescales)."""
+    L, MB, MS = W.WG_LMAX, 2, 300
+    beta = np.array([0.05, 1.0, math.pi / 2, math.pi - 0.05])
+    a = I.sky_alm(L, MS, 12)
+    b = I.beam_blm(L, MB, fwhm=0.001)
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form="fp32x").cpu().numpy()
+    W.check_device_status()
+    rng = np.random.default_rng(1)
+    idx = np.stack([rng.integers(0, MB + 1, 48), rng.integers(0, MS + 1, 48), rng.integers(0, beta.size, 48)], 1)
+    ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
+    assert _rel_l2(C[idx[:, 0], idx[:, 1], idx[:, 2]], ref) <= 1e-4
+
+    L, MB, MS = 2100, 2000, 2000
+    beta = np.array([0.02, 0.7, math.pi / 2, 2.5, math.pi - 0.02])
+    a = I.sky_alm(L, MS, 13)
+    rng = np.random.default_rng(14)
+    b = rng.standard_normal((L + 1, MB + 1)) + 1j * rng.standard_normal((L + 1, MB + 1))
+    b[np.arange(MB + 1)[None, :] > np.arange(L + 1)[:, None]] = 0
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form="fp32x").cpu().numpy()
+    W.check_device_status()
+    assert np.all(np.isfinite(C))
+    idx = np.array([[2000, 2000, j] for j in range(5)] + [[1999, 2000, 0], [2000, 1999, 4], [1500, 1800, 1],
+                                                          [1800, 1500, 3], [0, 2000, 2], [2000, 0, 1]])
+    ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
+    assert _rel_l2(C[idx[:, 0], idx[:, 1], idx[:, 2]], ref) <= 1e-4

@@ -118,3 +118,53 @@ def test_conv_l4096_sampled(W, form):
     ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
     assert np.max(np.abs(got - ref)) <= TOL
     assert np.all(np.isfinite(C.cpu().numpy()))
+
+
+def _random_beam(L, MB, seed):
+    """Complex beam weights of order one for every m_b <= min(l, MB) (a stress input whose
+    high-m_b columns do not vanish, unlike the Gaussian beam's)."""
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal((L + 1, MB + 1)) + 1j * rng.standard_normal((L + 1, MB + 1))
+    b[np.arange(MB + 1)[None, :] > np.arange(L + 1)[:, None]] = 0
+    return b / np.sqrt(L + 1.0)
+
+
+def _sample_idx(MB, MS, NB, n, seed, extra):
+    rng = np.random.default_rng(seed)
+    idx = np.stack([rng.integers(0, MB + 1, n), rng.integers(0, MS + 1, n), rng.integers(0, NB, n)], 1)
+    idx[:len(extra)] = extra
+    return idx
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_conv_longest_chains_sampled(W, form):
+    """The longest chains the library accepts (l_max = WG_LMAX = 32767), 301 sky orders, a
+    near-pole angle; sampled outputs against the oracle."""
+    L, MB, MS = W.WG_LMAX, 2, 300
+    beta = np.array([0.05, 1.0, math.pi / 2, math.pi - 0.05])
+    a = I.sky_alm(L, MS, 12)
+    b = I.beam_blm(L, MB, fwhm=0.001)
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form=form).cpu().numpy()
+    W.check_device_status()
+    idx = _sample_idx(MB, MS, beta.size, 48, 1,
+                      [[0, 0, 0], [2, 300, 0], [0, 0, 3], [2, 300, 3], [1, 150, 2], [2, 2, 1]])
+    ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
+    assert np.max(np.abs(C[idx[:, 0], idx[:, 1], idx[:, 2]] - ref)) <= TOL
+    assert np.all(np.isfinite(C))
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_conv_large_equal_orders_sampled(W, form):
+    """Chains starting at l0 = m_b = m_sky ~ 2000 (the largest coefficients F0 ~ l0 of the
+    first steps) and the whole 2001 x 2001 column range; sampled outputs."""
+    L, MB, MS = 2100, 2000, 2000
+    beta = np.array([0.02, 0.7, math.pi / 2, 2.5, math.pi - 0.02])
+    a = I.sky_alm(L, MS, 13)
+    b = _random_beam(L, MB, 14)
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form=form).cpu().numpy()
+    W.check_device_status()
+    extra = [[2000, 2000, j] for j in range(5)] + [[1999, 2000, 0], [2000, 1999, 4], [0, 2000, 2], [2000, 0, 1]]
+    idx = _sample_idx(MB, MS, beta.size, 60, 2, extra)
+    ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
+    assert np.max(np.abs(C[idx[:, 0], idx[:, 1], idx[:, 2]] - ref)) <= TOL
+    assert np.all(np.isfinite(C))
