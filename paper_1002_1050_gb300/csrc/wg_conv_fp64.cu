@@ -7,16 +7,25 @@
 namespace wg {
 
 template <int NT, int CPT, int TL, bool SUM_FF>
-__global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
+__global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int n_chunks, int group,
+                                                       const __grid_constant__ WeightMaps wm) {
     __shared__ SmemFp64<TL> sm;
+    __shared__ SmemTma<TL> st;
     const int item = blockIdx.x;
     const int chunk = item % n_chunks;
     const int grp = item / n_chunks;
     const int ncol = (A.mb_max + 1) * (A.ms_max + 1);
     const int k_begin = grp * group;
     const int k_end = min(ncol, k_begin + group);
+    if (threadIdx.x == 0) {
+        mbar_init(&st.mbar[0], 1);
+        mbar_init(&st.mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned ph[2] = {0u, 0u};
     unsigned long long n_elem = 0, n_sum = 0;
-    conv_fp64_item<NT, CPT, TL, SUM_FF>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum);
+    conv_fp64_item<NT, CPT, TL, SUM_FF, true>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum, &wm, &st, ph);
     flush_counters(A.counters, n_elem, n_sum);
 }
 
@@ -29,7 +38,10 @@ static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, 
     const long long items = (long long)n_chunks * n_groups;
     if (items == 0) return 0;
     if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-    conv_fp64_kernel<NT, CPT, TL, SUM_FF><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group);
+    WeightMaps wm;
+    const int e = encode_weight_maps(a.a, a.b, a.l_max, a.mb_max, a.ms_max, TL, &wm);
+    if (e != 0) return e;
+    conv_fp64_kernel<NT, CPT, TL, SUM_FF><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group, wm);
     return (int)cudaGetLastError();
 }
 

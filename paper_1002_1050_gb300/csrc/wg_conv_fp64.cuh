@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "wg_common.cuh"
+#include "wg_tma.cuh"
 
 namespace wg {
 
@@ -57,15 +58,28 @@ struct SmemFp64 {
     double sSig[TL + 1];   // sigma_{ts + i}
 };
 
+// TMA staging of the weights: two buffers of the l-tile's a and b boxes (the tile after
+// next is requested as soon as a buffer's tile has been read), one mbarrier each.
+template <int TL>
+struct SmemTma {
+    alignas(128) double2 sAw[2][TL];
+    alignas(128) double2 sBw[2][TL];
+    unsigned long long mbar[2];
+};
+
 __device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
     hi = __double2float_rn(x);
     lo = __double2float_rn(x - (double)hi);
 }
 
-template <int NT, int CPT, int TL, bool SUM_FF>
-__device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
+// TMA: the weights arrive by TMA (wm, st; the mbarriers initialised by the caller, their
+// phases in ph), else by plain loads.  Returns false if a TMA wait gave up (the status
+// word then has WG_DEVERR_TIMEOUT and no copy is left in flight).
+template <int NT, int CPT, int TL, bool SUM_FF, bool TMA = false>
+__device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
                                                  int k_end, SmemFp64<TL> &sm, unsigned long long &n_elem,
-                                                 unsigned long long &n_sum) {
+                                                 unsigned long long &n_sum, const WeightMaps *wm = nullptr,
+                                                 SmemTma<TL> *st = nullptr, unsigned *ph = nullptr) {
     const int MB1 = A.mb_max + 1;
     const int L = A.l_max;
     const int NB = A.n_beta;
@@ -106,17 +120,52 @@ __device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &
         }
         bool warp_sum = false;
         double sig_m1 = 0.0, sig_0 = 1.0;  // thread 0's carry: sigma_{ts-1}, sigma_{ts}
+        bool inflight[2] = {false, false};  // TMA: a tile requested and not yet waited for
+        if (TMA) {
+            if (tid == 0) {
+                tma_weights<TL>(wm, mb, ms, l0, st->sAw[0], st->sBw[0], &st->mbar[0]);
+                if (l0 + TL <= L) tma_weights<TL>(wm, mb, ms, l0 + TL, st->sAw[1], st->sBw[1], &st->mbar[1]);
+            }
+            inflight[0] = true;
+            inflight[1] = l0 + TL <= L;
+        }
 
-        for (int ts = l0; ts <= L; ts += TL) {
-            __syncthreads();
+        int tix = 0;
+        for (int ts = l0; ts <= L; ts += TL, ++tix) {
+            const int buf = tix & 1;
+            bool ok = true;
+            if (TMA) {
+                ok = mbar_wait(&st->mbar[buf], ph[buf]);
+                if (ok) {
+                    inflight[buf] = false;
+                    ph[buf] ^= 1u;
+                }
+            }
+            if (!__syncthreads_and(ok)) {
+                // a TMA wait gave up: record it, give the copies in flight a bounded
+                // chance to land, and leave
+                if (tid == 0) {
+                    raise_status(T.status, WG_DEVERR_TIMEOUT);
+                    for (int b2 = 0; b2 < 2; ++b2)
+                        if (inflight[b2]) mbar_wait(&st->mbar[b2], ph[b2]);
+                }
+                __syncthreads();
+                return false;
+            }
             for (int i = tid; i < TL; i += NT) {  // phase 1: F0, G, F2, w
                 const int l = ts + i;
                 double f0 = 0.0, g = 0.0, f2 = 0.0;
                 double2 w = make_double2(0.0, 0.0);
                 if (l <= L) {
                     if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
-                    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
-                    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+                    double2 av, bv;
+                    if (TMA) {
+                        av = st->sAw[buf][i];
+                        bv = st->sBw[buf][i];
+                    } else {
+                        av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
+                        bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+                    }
                     w = make_double2(bv.x * av.x + bv.y * av.y, bv.x * av.y - bv.y * av.x);
                 }
                 sm.sA[i] = make_double2(f0, g);
@@ -124,6 +173,10 @@ __device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &
                 sm.sWd[i] = w;
             }
             __syncthreads();
+            if (TMA && ts + 2 * TL <= L) {  // this buffer has been read: request the tile after next
+                if (tid == 0) tma_weights<TL>(wm, mb, ms, ts + 2 * TL, st->sAw[buf], st->sBw[buf], &st->mbar[buf]);
+                inflight[buf] = true;
+            }
             if (tid == 0) {  // phase 2: sigma_{ts+i}, i = 0..TL
                 double sm1 = sig_m1, s0 = sig_0;
                 sm.sSig[0] = s0;
@@ -228,6 +281,7 @@ __device__ __forceinline__ void conv_fp64_item(const ConvArgs &A, const Tables &
             }
         }
     }
+    return true;
 }
 
 // warp-aggregated counter update (one atomic per warp)
