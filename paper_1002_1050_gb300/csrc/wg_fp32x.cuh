@@ -364,7 +364,7 @@ __device__ __forceinline__ void normalise_tile(SmemFp32<NT, CPT, TL> &sm, int bu
             s_n = so.hi;
         }
         const float4 w = sm.sW[buf][e];
-        const float rho = __fdiv_rn(s_e, s_n);
+        const float rho = __fdividef(s_e, s_n);  // a float coefficient's accuracy suffices
         const float f0p = r.x * rho, gp = r.y * rho;
         const float wr = w.x * s_e, wi = w.z * s_e;
         sm.sN[e] = (e < nl) ? make_float4(f0p, f0p, -gp, -gp) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -376,9 +376,10 @@ __device__ __forceinline__ void normalise_tile(SmemFp32<NT, CPT, TL> &sm, int bu
 }
 
 // the K pair of each chain pair at tile entry i: the thread's common K (UNIFORM: all its
-// chains on the same side of pi/2) or each chain's own (hoff = 2 for a mirrored chain)
+// chains on the same side of pi/2) or each chain's own (bit c of hbits: chain c is
+// mirrored and takes K1, at index 2 of (K0, K0, K1, K1))
 template <int NP, bool UNIFORM>
-__device__ __forceinline__ void k_pairs(const float4 &k4, int thigh, const int (&hoff)[2 * NP], float2 (&kp)[NP]) {
+__device__ __forceinline__ void k_pairs(const float4 &k4, int thigh, int hbits, float2 (&kp)[NP]) {
     if (UNIFORM) {
         const float2 k = reinterpret_cast<const float2 *>(&k4)[thigh];
 #pragma unroll
@@ -386,27 +387,28 @@ __device__ __forceinline__ void k_pairs(const float4 &k4, int thigh, const int (
     } else {
         const float *kq = reinterpret_cast<const float *>(&k4);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) kp[p] = make_float2(kq[hoff[2 * p]], kq[hoff[2 * p + 1]]);
+        for (int p = 0; p < NP; ++p)
+            kp[p] = make_float2(kq[((hbits >> (2 * p)) & 1) << 1], kq[((hbits >> (2 * p + 1)) & 1) << 1]);
     }
 }
 
 // The steps of one l-tile (nl orders) in the difference form for every chain of the thread.
 template <int NP, int TL, bool UNIFORM>
 __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, const float4 *sW, int nl, bool plain,
-                                           int thigh, const int (&hoff)[2 * NP], const float2 (&x2p)[NP],
+                                           int thigh, int hbits, const float2 (&x2p)[NP],
                                            float2 (&cur)[NP], float2 (&aux)[NP], int (&nsc)[2 * NP],
                                            float2 (&sp)[NP], float2 (&pr)[2][NP], float2 (&pi)[2][NP]) {
     float2 kp[NP];
     int i = 0;
     if (plain) {  // every chain of the warp is a plain float
         for (; i + 1 < nl; i += 2) {
-            k_pairs<NP, UNIFORM>(sK[i], thigh, hoff, kp);
+            k_pairs<NP, UNIFORM>(sK[i], thigh, hbits, kp);
             step_pairs<NP, 0, false>(sA[i], kp, sW[i], x2p, cur, aux, sp, pr, pi);
-            k_pairs<NP, UNIFORM>(sK[i + 1], thigh, hoff, kp);
+            k_pairs<NP, UNIFORM>(sK[i + 1], thigh, hbits, kp);
             step_pairs<NP, 1, false>(sA[i + 1], kp, sW[i + 1], x2p, cur, aux, sp, pr, pi);
         }
         if (i < nl) {
-            k_pairs<NP, UNIFORM>(sK[i], thigh, hoff, kp);
+            k_pairs<NP, UNIFORM>(sK[i], thigh, hbits, kp);
             step_pairs<NP, 0, false>(sA[i], kp, sW[i], x2p, cur, aux, sp, pr, pi);
         }
     } else {
@@ -414,22 +416,22 @@ __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, c
         for (; i + 3 < nl; i += 4) {
 #pragma unroll
             for (int q = 0; q < 4; q += 2) {
-                k_pairs<NP, UNIFORM>(sK[i + q], thigh, hoff, kp);
+                k_pairs<NP, UNIFORM>(sK[i + q], thigh, hbits, kp);
                 step_pairs<NP, 0, true>(sA[i + q], kp, sW[i + q], x2p, cur, aux, sp, pr, pi);
-                k_pairs<NP, UNIFORM>(sK[i + q + 1], thigh, hoff, kp);
+                k_pairs<NP, UNIFORM>(sK[i + q + 1], thigh, hbits, kp);
                 step_pairs<NP, 1, true>(sA[i + q + 1], kp, sW[i + q + 1], x2p, cur, aux, sp, pr, pi);
             }
             rescale_pairs(cur, aux, nsc, sp);
         }
         if (i < nl) {
-            k_pairs<NP, UNIFORM>(sK[i], thigh, hoff, kp);
+            k_pairs<NP, UNIFORM>(sK[i], thigh, hbits, kp);
             step_pairs<NP, 0, true>(sA[i], kp, sW[i], x2p, cur, aux, sp, pr, pi);
             if (i + 1 < nl) {
-                k_pairs<NP, UNIFORM>(sK[i + 1], thigh, hoff, kp);
+                k_pairs<NP, UNIFORM>(sK[i + 1], thigh, hbits, kp);
                 step_pairs<NP, 1, true>(sA[i + 1], kp, sW[i + 1], x2p, cur, aux, sp, pr, pi);
             }
             if (i + 2 < nl) {
-                k_pairs<NP, UNIFORM>(sK[i + 2], thigh, hoff, kp);
+                k_pairs<NP, UNIFORM>(sK[i + 2], thigh, hbits, kp);
                 step_pairs<NP, 0, true>(sA[i + 2], kp, sW[i + 2], x2p, cur, aux, sp, pr, pi);
             }
             rescale_pairs(cur, aux, nsc, sp);
@@ -489,18 +491,21 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
     const int L = A.l_max;
     const int NB = A.n_beta;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int j0 = chunk * NT * CPT + tid;  // angle of chain c: j0 + c * NT
+    // a thread's chains are CPT adjacent angles, a warp's 32 CPT consecutive ones, so that
+    // only the warps that hold angles near a pole take the difference form
+    const int j0 = chunk * NT * CPT + tid * CPT;  // angle of chain c: j0 + c
 
-    float2 x2p[NP];   // x^2 of the difference form (sin^2 or, mirrored, cos^2 of beta/2)
-    float2 cbp[NP];   // cos(beta) (normalised form)
-    int hoff[CPT];    // 2 for a mirrored chain (index of K1 in (K0, K0, K1, K1)), else 0
-    bool same = true, bulk = true;
+    int hbits = 0;    // bit c: chain c is mirrored (beta > pi/2)
+    bool bulk = true;
     const float sthr = bulk_sin_threshold(L);
+    float2 x2p[NP], cbp[NP];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        const bool valid = j0 + c * NT < NB;
-        const Angle32 t = make_angle32(valid ? A.beta[j0 + c * NT] : 1.0);
+        const bool valid = j0 + c < NB;
+        const Angle32 t = make_angle32(valid ? A.beta[j0 + c] : 1.0);
         if (valid && t.bad) raise_status(T.status, WG_DEVERR_BETA);
+        hbits |= (t.high ? 1 : 0) << c;
+        bulk = bulk && (t.sb >= sthr) && !t.bad;
         if (c & 1) {
             x2p[c / 2].y = t.x2;
             cbp[c / 2].y = t.cb;
@@ -508,15 +513,19 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             x2p[c / 2].x = t.x2;
             cbp[c / 2].x = t.cb;
         }
-        hoff[c] = t.high ? 2 : 0;
-        same = same && (hoff[c] == hoff[0]);
-        bulk = bulk && (t.sb >= sthr) && !t.bad;
         sm.sLog[c][tid] = make_float4(t.lnc.hi, t.lnc.lo, t.lns.hi, t.lns.lo);
         sm.sFlag[c][tid] = (t.bad ? 1 : 0) | (t.high ? 2 : 0) | (t.c_zero ? 4 : 0) | (t.s_zero ? 8 : 0);
     }
-    const int thigh = hoff[0] >> 1;                          // the thread's side when `same`
+    const int thigh = hbits & 1;                             // the thread's side when uniform
+    const bool same = hbits == 0 || hbits == (1 << CPT) - 1;
     const bool uniform = __all_sync(0xffffffffu, same);      // warp-uniform code paths
     const bool wbulk = __all_sync(0xffffffffu, bulk);
+    // one float per chain stays live: cos(beta) for warps of the normalised form (whose
+    // rare columns from l0 >= 8192 take x^2 = (1 - |cos beta|) / 2, accurate there as
+    // sin(beta) >= 0.1), x^2 for the others
+    float2 xr[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) xr[p] = wbulk ? cbp[p] : x2p[p];
 
     for (int k = k_begin; k < k_end; ++k) {
         const int ms = k / MB1, mb = k - ms * MB1;
@@ -525,6 +534,11 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
         const bool need_norm = __syncthreads_or(norm) != 0;
 
         float2 cur[NP], aux[NP], sp[NP], pr[2][NP], pi[2][NP];
+        float2 xv[NP];  // per chain: cos(beta) (normalised form) or x^2 (difference form)
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+            xv[p] = (norm || !wbulk) ? xr[p]
+                                     : make_float2(0.5f * (1.0f - fabsf(xr[p].x)), 0.5f * (1.0f - fabsf(xr[p].y)));
         int nsc[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
@@ -551,7 +565,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 sp[c / 2].x = spv;
             }
             nsc[c] = s.n;
-            if (s.n == 0 && j0 + c * NT < NB) n_sum += (unsigned long long)(L + 1 - l0);
+            if (s.n == 0 && j0 + c < NB) n_sum += (unsigned long long)(L + 1 - l0);
             sm.sAcc[c][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         bool warp_plain = false;
@@ -587,26 +601,26 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                         au *= 0x1p-64f;
                         su = 1.0f;
                         nsc[c] = 0;
-                        if (j0 + c * NT < NB) n_sum += (unsigned long long)(L + 1 - ts);
+                        if (j0 + c < NB) n_sum += (unsigned long long)(L + 1 - ts);
                     }
                     p = p && (nsc[c] == 0);
                 }
                 warp_plain = __all_sync(0xffffffffu, p);
             }
             if (norm)
-                tile_steps_norm<NP, TL>(sm.sN, sm.sWn, nl, warp_plain, cbp, cur, aux, nsc, sp, pr, pi);
+                tile_steps_norm<NP, TL>(sm.sN, sm.sWn, nl, warp_plain, xv, cur, aux, nsc, sp, pr, pi);
             else if (uniform)
-                tile_steps<NP, TL, true>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hoff, x2p, cur,
+                tile_steps<NP, TL, true>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hbits, xv, cur,
                                          aux, nsc, sp, pr, pi);
             else
-                tile_steps<NP, TL, false>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hoff, x2p, cur,
+                tile_steps<NP, TL, false>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hbits, xv, cur,
                                           aux, nsc, sp, pr, pi);
             // partials of this tile into the compensated sums; the sign of the odd-offset
             // partial is (-1) for mirrored chains of the difference form, and the tile's
             // start parity (that of l0, as TL is even) is applied at the end
 #pragma unroll
             for (int c = 0; c < CPT; ++c) {
-                const float sg = (hoff[c] && !norm) ? -1.f : 1.f;
+                const float sg = (((hbits >> c) & 1) && !norm) ? -1.f : 1.f;
                 const float p0r = (c & 1) ? pr[0][c / 2].y : pr[0][c / 2].x;
                 const float p1r = (c & 1) ? pr[1][c / 2].y : pr[1][c / 2].x;
                 const float p0i = (c & 1) ? pi[0][c / 2].y : pi[0][c / 2].x;
@@ -633,7 +647,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
         double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
-            const int j = j0 + c * NT;
+            const int j = j0 + c;
             if (j < NB) {
                 const int fl = sm.sFlag[c][tid];
                 const float4 acc = sm.sAcc[c][tid];

@@ -141,3 +141,23 @@ def test_conv_fp32x_size_limits_sampled(W):
                                                           [1800, 1500, 3], [0, 2000, 2], [2000, 0, 1]])
     ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
     assert _rel_l2(C[idx[:, 0], idx[:, 1], idx[:, 2]], ref) <= 1e-4
+
+
+def test_conv_fp32x_columns_from_l0_8192(W):
+    """Away from the poles the FP32 form runs the normalised recursion, except for
+    columns starting at l0 >= 8192 (difference form, x^2 derived from cos(beta)); a sum
+    whose columns straddle that limit, sampled against the oracle."""
+    L, MB, MS = 8250, 0, 8250
+    beta = np.array([1.45, 1.52, 1.6, 1.68])  # near pi/2: the orders m_sky ~ 8200 reach their turning point
+    a = I.sky_alm(L, MS, 15)
+    b = I.beam_blm(L, MB, fwhm=0.0005)
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form="fp32x").cpu().numpy()
+    W.check_device_status()
+    assert np.all(np.isfinite(C))
+    ms = [0, 100, 4000, 8100, 8191, 8192, 8193, 8200, 8249, 8250]
+    idx = np.array([[0, m, j] for m in ms for j in range(beta.size)])
+    ref = O.conv_sum_sampled(L, MB, MS, beta, a, b, idx)
+    got = C[idx[:, 0], idx[:, 1], idx[:, 2]]
+    assert _rel_l2(got, ref) <= 1e-4
+    hi = idx[:, 1] >= 8192  # the difference-form columns on their own
+    assert _rel_l2(got[hi], ref[hi]) <= 1e-4
