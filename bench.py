@@ -241,10 +241,15 @@ def run_ours(args):
     h2d = beta_p.numel() * 8 + a_p.numel() * 16 + b_p.numel() * 16
     d2h = c_p.numel() * 16
 
+    # device buffers the inputs are copied into every step (allocated once, as a caller would)
+    bd = torch.empty_like(beta)
+    ad = torch.empty_like(a)
+    bbd = torch.empty_like(b)
+
     def e2e_step():
-        bd = beta_p.to(dev, non_blocking=True)
-        ad = a_p.to(dev, non_blocking=True)
-        bbd = b_p.to(dev, non_blocking=True)
+        bd.copy_(beta_p, non_blocking=True)
+        ad.copy_(a_p, non_blocking=True)
+        bbd.copy_(b_p, non_blocking=True)
         W.wigner_conv_sum(bd, ad, bbd, out=out)
         c_p.copy_(out, non_blocking=True)
 
