@@ -276,101 +276,103 @@ __device__ __forceinline__ void step_norm(const float4 n4, const float4 w4, cons
 // logarithms and flags, and the Neumaier-compensated sums.
 template <int NT, int CPT, int TL>
 struct SmemFp32 {
-    static_assert(TL <= NT && TL % 32 == 0, "one tile entry per thread of the first TL / 32 warps");
     float4 sA[2][TL];       // (A, A, F2, F2), A = -2 F0
     float4 sK[2][TL];       // (K0, K0, K1, K1)
     float4 sW[2][TL];       // (w_re, w_re, w_im, w_im)
+    float4 sRaw[TL];        // (F0, G, F2 hi, F2 lo) of the tile being built
     float4 sN[TL];          // (F0', F0', -G', -G') of the normalised form
     float4 sWn[TL];         // (w sigma)(re, re, im, im)
-    float4 sTot[TL / 32];   // per warp of entries: product of F2 over its even, odd entries (float-float)
-    float4 sSig[2];         // sigma at the entries -1 and 0 of a tile (float-float), by tile parity
+    float4 sSig;            // sigma at the entries -1 and 0 of the next tile (float-float)
     float4 sLog[CPT][NT];   // (ln cos(b/2) hi, lo, ln sin(b/2) hi, lo)
     int sFlag[CPT][NT];     // bit 0: bad angle, 1: mirrored, 2: cos(b/2) = 0, 3: sin(b/2) = 0
     float4 sAcc[CPT][NT];   // compensated sums (re, re carry, im, im carry)
 };
 
-// One thread's entry e (< TL) of a tile starting at ts: the difference form's operands
-// into buffer buf, and the values the normalised form needs kept in the thread (raw F0,
-// G, F2 as float-float, w).  F2 of the first order l0 is entered as 1 (sigma_{l0+1} =
-// sigma_{l0}), as is F2 past l_max.  With `norm`, the warp then scans F2 along each
-// parity of the entries (sigma_{e+1} = F2_e sigma_{e-1}) and posts its totals.
-struct TileEntry {
-    float f0, g, wr, wi;
-    ff pre;  // product of F2 over this warp's entries e' <= e of e's parity
-};
-
+// operands of order l (<= L) of column (mb, ms) into tile entry i of buffer buf; F2 of
+// the first order l0 is entered as 1 (sigma_{l0+1} = sigma_{l0}), as is F2 past l_max
 template <int NT, int CPT, int TL>
-__device__ __forceinline__ TileEntry build_tile_entry(const ConvArgs &A, const Tables &T, int ts, int l0, int mb,
-                                                      int ms, SmemFp32<NT, CPT, TL> &sm, int buf, bool norm) {
-    const int e = threadIdx.x, lane = e & 31;
-    const int l = ts + e;
-    TileEntry r{0.f, 0.f, 0.f, 0.f, ff{1.0f, 0.0f}};
-    ff f2{1.0f, 0.0f};
-    if (l <= A.l_max) {
-        const int MB1 = A.mb_max + 1;
-        const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
-        const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
-        const float ar = d2f_trunc(av.x), ai = d2f_trunc(av.y);
-        const float br = d2f_trunc(bv.x), bi = d2f_trunc(bv.y);
-        r.wr = __fmaf_rn(br, ar, bi * ai);
-        r.wi = __fmaf_rn(br, ai, -(bi * ar));
-        float4 raw;
-        const float4 c = diff_coefficients(l, A.l_max, mb, ms, T, raw);
-        r.f0 = raw.x;
-        r.g = raw.y;
-        if (l != l0) f2 = ff{raw.z, raw.w};
-        sm.sA[buf][e] = make_float4(c.x, c.x, c.y, c.y);
-        sm.sK[buf][e] = make_float4(c.z, c.z, c.w, c.w);
-        sm.sW[buf][e] = make_float4(r.wr, r.wr, r.wi, r.wi);
+__device__ __forceinline__ void build_tile_entry(const ConvArgs &A, const Tables &T, int l, int l0, int mb, int ms,
+                                                 SmemFp32<NT, CPT, TL> &sm, int buf, int i) {
+    const int MB1 = A.mb_max + 1;
+    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
+    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+    const float ar = d2f_trunc(av.x), ai = d2f_trunc(av.y);
+    const float br = d2f_trunc(bv.x), bi = d2f_trunc(bv.y);
+    const float wr = __fmaf_rn(br, ar, bi * ai), wi = __fmaf_rn(br, ai, -(bi * ar));
+    float4 raw;
+    const float4 c = diff_coefficients(l, A.l_max, mb, ms, T, raw);
+    if (l == l0) {
+        raw.z = 1.0f;
+        raw.w = 0.0f;
     }
-    if (norm) {
-        // inclusive product over the lanes of the same parity (entry parity = lane parity)
-        ff v = f2;
-#pragma unroll
-        for (int off = 2; off < 32; off <<= 1) {
-            const ff u{__shfl_up_sync(0xffffffffu, v.hi, off), __shfl_up_sync(0xffffffffu, v.lo, off)};
-            if (lane >= off) v = ff_mul(v, u);
-        }
-        r.pre = v;
-        const ff te{__shfl_sync(0xffffffffu, v.hi, 30), __shfl_sync(0xffffffffu, v.lo, 30)};
-        const ff to{__shfl_sync(0xffffffffu, v.hi, 31), __shfl_sync(0xffffffffu, v.lo, 31)};
-        if (lane == 0) sm.sTot[e >> 5] = make_float4(te.hi, te.lo, to.hi, to.lo);
-    }
-    return r;
+    sm.sA[buf][i] = make_float4(c.x, c.x, c.y, c.y);
+    sm.sK[buf][i] = make_float4(c.z, c.z, c.w, c.w);
+    sm.sW[buf][i] = make_float4(wr, wr, wi, wi);
+    sm.sRaw[i] = raw;
 }
 
-// After a barrier: the normalised form's operands of this thread's entry e, from the
-// warp prefix, the totals of the warps before and the tile's carry sSig[par] (sigma at
-// the entries -1 and 0); the last warp's lanes 30 and 31 leave the next tile's carry
-// in sSig[par ^ 1].  sigma_{e+1} = P_e sigma_{-1} (e even) or P_e sigma_0 (e odd), with
-// P_e the product of F2 over the entries e' <= e of e's parity; sigma_e likewise from
-// P_{e-1}, taken from the lane before.
+// The normalised form's operands of a built tile, by one warp: sigma over the tile by
+// a float-float product scan of F2 along each parity of l, sigma_{e+1} = F2_e
+// sigma_{e-1} (carry in sSig: sigma at the entries -1 and 0, replaced by the next
+// tile's), then rho = sigma_e / sigma_{e+1}, F0' = F0 rho, G' = G rho, w sigma.  Lane t
+// owns entries EPL t .. EPL t + EPL - 1.
 template <int NT, int CPT, int TL>
-__device__ __forceinline__ void normalise_entry(SmemFp32<NT, CPT, TL> &sm, const TileEntry &r, int par, int nl) {
-    const int e = threadIdx.x, lane = e & 31, w = e >> 5;
-    ff pe{1.0f, 0.0f}, po{1.0f, 0.0f};  // products of the earlier warps' even, odd entries
-    for (int k = 0; k < w; ++k) {
-        const float4 t = sm.sTot[k];
-        pe = ff_mul(pe, ff{t.x, t.y});
-        po = ff_mul(po, ff{t.z, t.w});
+__device__ __forceinline__ void normalise_tile(SmemFp32<NT, CPT, TL> &sm, int buf, int nl, int lane) {
+    constexpr int EPL = TL / 32;
+    static_assert(TL % 64 == 0, "an even number of entries per lane");
+    const int e0 = EPL * lane;
+    // products of the lane's factors on each parity chain
+    ff pe{1.0f, 0.0f}, po{1.0f, 0.0f};  // factors of odd entries (even chain), of even entries (odd chain)
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+        const float4 r = sm.sRaw[e0 + q];
+        const ff f = (e0 + q < nl) ? ff{r.z, r.w} : ff{1.0f, 0.0f};
+        if (q & 1)
+            pe = ff_mul(pe, f);
+        else
+            po = ff_mul(po, f);
     }
-    const float4 cs = sm.sSig[par];
-    const ff sm1{cs.x, cs.y}, s0{cs.z, cs.w};
-    // P_e over the whole tile, then sigma_{e+1}
-    const ff pfull = ff_mul(r.pre, (lane & 1) ? po : pe);
-    const ff s_next = ff_mul(pfull, (lane & 1) ? s0 : sm1);
-    // sigma_e = sigma_{(e-1)+1}: from lane - 1, or for lane 0 from the odd product of the
-    // earlier warps (entry e - 1 is odd)
-    ff s_e{__shfl_up_sync(0xffffffffu, s_next.hi, 1), __shfl_up_sync(0xffffffffu, s_next.lo, 1)};
-    if (lane == 0) s_e = ff_mul(po, s0);
-    const float rho = __fdividef(s_e.hi, s_next.hi);  // a float coefficient's accuracy suffices
-    const float f0p = r.f0 * rho, gp = r.g * rho;
-    const float wr = r.wr * s_e.hi, wi = r.wi * s_e.hi;
-    sm.sN[e] = (e < nl) ? make_float4(f0p, f0p, -gp, -gp) : make_float4(0.f, 0.f, 0.f, 0.f);
-    sm.sWn[e] = (e < nl) ? make_float4(wr, wr, wi, wi) : make_float4(0.f, 0.f, 0.f, 0.f);
-    // the next tile's carry: sigma_{TL-1} (= s_next of entry TL - 2) and sigma_TL (of TL - 1)
-    const ff c_m1{__shfl_sync(0xffffffffu, s_next.hi, 30), __shfl_sync(0xffffffffu, s_next.lo, 30)};
-    if (e == TL - 1) sm.sSig[par ^ 1] = make_float4(c_m1.hi, c_m1.lo, s_next.hi, s_next.lo);
+    // inclusive product scans over the lanes, then exclusive
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const ff e{__shfl_up_sync(0xffffffffu, pe.hi, off), __shfl_up_sync(0xffffffffu, pe.lo, off)};
+        const ff o{__shfl_up_sync(0xffffffffu, po.hi, off), __shfl_up_sync(0xffffffffu, po.lo, off)};
+        if (lane >= off) {
+            pe = ff_mul(pe, e);
+            po = ff_mul(po, o);
+        }
+    }
+    ff xe{__shfl_up_sync(0xffffffffu, pe.hi, 1), __shfl_up_sync(0xffffffffu, pe.lo, 1)};
+    ff xo{__shfl_up_sync(0xffffffffu, po.hi, 1), __shfl_up_sync(0xffffffffu, po.lo, 1)};
+    if (lane == 0) xe = xo = ff{1.0f, 0.0f};
+    const float4 carry = sm.sSig;
+    ff se = ff_mul(ff{carry.z, carry.w}, xe);  // sigma at the lane's first entry (even)
+    ff so = ff_mul(ff{carry.x, carry.y}, xo);  // sigma at the entry before it (odd)
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+        const int e = e0 + q;
+        const float4 r = sm.sRaw[e];
+        const ff f = (e < nl) ? ff{r.z, r.w} : ff{1.0f, 0.0f};
+        float s_e, s_n;  // sigma_e, sigma_{e+1}
+        if (q & 1) {
+            s_e = so.hi;
+            se = ff_mul(se, f);
+            s_n = se.hi;
+        } else {
+            s_e = se.hi;
+            so = ff_mul(so, f);
+            s_n = so.hi;
+        }
+        const float4 w = sm.sW[buf][e];
+        const float rho = __fdividef(s_e, s_n);  // a float coefficient's accuracy suffices
+        const float f0p = r.x * rho, gp = r.y * rho;
+        const float wr = w.x * s_e, wi = w.z * s_e;
+        sm.sN[e] = (e < nl) ? make_float4(f0p, f0p, -gp, -gp) : make_float4(0.f, 0.f, 0.f, 0.f);
+        sm.sWn[e] = (e < nl) ? make_float4(wr, wr, wi, wi) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // carry: sigma at the tile's last two entries (lane 31: so = sigma_{TL-1}, se = sigma_{TL})
+    __syncwarp();
+    if (lane == 31) sm.sSig = make_float4(so.hi, so.lo, se.hi, se.lo);
 }
 
 // the K pair of each chain pair at tile entry i: the thread's common K (UNIFORM: all its
@@ -567,17 +569,15 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             sm.sAcc[c][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         bool warp_plain = false;
-        if (tid == 0) sm.sSig[0] = make_float4(1.0f, 0.0f, 1.0f, 0.0f);  // sigma_{l0-1} (entered as 1), sigma_{l0}
+        if (tid == 0) sm.sSig = make_float4(1.0f, 0.0f, 1.0f, 0.0f);  // sigma_{l0-1} (entered as 1), sigma_{l0}
 
-        // first tile's operands into buffer 0 (threads tid < TL own one entry each)
-        {
-            TileEntry te{};
-            if (tid < TL) te = build_tile_entry<NT, CPT, TL>(A, T, l0, l0, mb, ms, sm, 0, need_norm);
+        // first tile's operands into buffer 0
+        for (int i = tid; i < TL; i += NT)
+            if (l0 + i <= L) build_tile_entry<NT, CPT, TL>(A, T, l0 + i, l0, mb, ms, sm, 0, i);
+        __syncthreads();
+        if (need_norm) {
+            if (tid < 32) normalise_tile<NT, CPT, TL>(sm, 0, min(TL, L + 1 - l0), lane);
             __syncthreads();
-            if (need_norm) {
-                if (tid < TL) normalise_entry<NT, CPT, TL>(sm, te, 0, min(TL, L + 1 - l0));
-                __syncthreads();
-            }
         }
 
         int buf = 0;
@@ -632,15 +632,14 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             }
             // the next tile: its operands into the other buffer (their previous readers
             // passed the barrier at the end of the last tile), a barrier, then the
-            // normalised form's operands (each thread its own entry) and a second barrier
+            // normalised form's operands (one warp) and a second barrier
             const int tn = ts + TL;
             if (tn <= L) {
-                const int par = ((tn - l0) / TL) & 1;  // parity of the next tile's index
-                TileEntry te{};
-                if (tid < TL) te = build_tile_entry<NT, CPT, TL>(A, T, tn, l0, mb, ms, sm, buf ^ 1, need_norm);
+                for (int i = tid; i < TL; i += NT)
+                    if (tn + i <= L) build_tile_entry<NT, CPT, TL>(A, T, tn + i, l0, mb, ms, sm, buf ^ 1, i);
                 __syncthreads();
                 if (need_norm) {
-                    if (tid < TL) normalise_entry<NT, CPT, TL>(sm, te, par, min(TL, L + 1 - tn));
+                    if (tid < 32) normalise_tile<NT, CPT, TL>(sm, buf ^ 1, min(TL, L + 1 - tn), lane);
                     __syncthreads();
                 }
             }
