@@ -107,11 +107,31 @@ int wigner_d_table_backward(int l_max, int mb_max, int ms_max, int n_beta, const
  *   b: beam coefficients b[l][mb], wg_c64, shape (l_max+1, mb_max+1), 16-byte aligned.
  *   c_out[mb][ms][j] = sum_{l >= max(mb,ms)} conj(b[l][mb]) a[l][ms] d^l_{mb,ms}(beta_j),
  *   wg_c64, shape (mb_max+1, ms_max+1, n_beta), overwritten.
- *   form: WG_FP64 or WG_FP32X.  counters: optional.
+ *   form: WG_FP64, WG_FP64S or WG_FP32X.  counters: optional.
+ *   In the FP64 forms the l-ordered weights reach shared memory by TMA, so a and b must
+ *   also have row pitches that are multiples of 16 bytes (always true for wg_c64 rows).
  * ------------------------------------------------------------------------- */
 int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
                     const wg_c64 *a, const wg_c64 *b, wg_form form, wg_c64 *c_out,
                     wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * wigner_conv_sum_host -- wigner_conv_sum (Sec. 4.1 Eq. convdef) on HOST buffers.
+ *   beta_host, a_host, b_host, c_host: host memory with the layouts of wigner_conv_sum;
+ *   page-locked (cudaHostAlloc / pinned) memory lets the copies overlap the computation,
+ *   pageable memory works but is copied synchronously.
+ *   The inputs are uploaded on `stream`; the chain columns are then computed in four
+ *   launches over blocks of sky orders of about equal work, and each block's slice of C
+ *   is downloaded on a library-owned stream while the next block computes.  On return
+ *   all work is enqueued and `stream` waits for the downloads: synchronise `stream`
+ *   before reading c_host.  The host buffers must stay valid until then.
+ *   Device buffers come from a library-owned stream-ordered pool (allocated on first use,
+ *   kept for later calls), so calls on different streams may run concurrently.
+ *   Errors: as wigner_conv_sum (NULL host buffers: WG_ERR_ARG; no room: WG_ERR_ALLOC).
+ * ------------------------------------------------------------------------- */
+int wigner_conv_sum_host(int l_max, int mb_max, int ms_max, int n_beta, const double *beta_host,
+                         const wg_c64 *a_host, const wg_c64 *b_host, wg_form form, wg_c64 *c_host,
+                         void *stream);
 
 /* ---------------------------------------------------------------------------
  * wigner_conv_sum_backward -- adjoint of wigner_conv_sum for a real loss L, in

@@ -15,8 +15,9 @@ __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int
     const int chunk = item % n_chunks;
     const int grp = item / n_chunks;
     const int ncol = (A.mb_max + 1) * (A.ms_max + 1);
-    const int k_begin = grp * group;
-    const int k_end = min(ncol, k_begin + group);
+    const int k_hi = A.k_hi < 0 ? ncol : A.k_hi;
+    const int k_begin = A.k_lo + grp * group;
+    const int k_end = min(k_hi, k_begin + group);
     if (threadIdx.x == 0) {
         mbar_init(&st.mbar[0], 1);
         mbar_init(&st.mbar[1], 1);
@@ -34,7 +35,8 @@ static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, 
     const int per_chunk = NT * CPT;
     const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
     const int ncol = (a.mb_max + 1) * (a.ms_max + 1);
-    const int n_groups = (ncol + group - 1) / group;
+    const int nk = (a.k_hi < 0 ? ncol : a.k_hi) - a.k_lo;
+    const int n_groups = (nk + group - 1) / group;
     const long long items = (long long)n_chunks * n_groups;
     if (items == 0) return 0;
     if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;

@@ -13,8 +13,9 @@ __global__ void __launch_bounds__(NT, 6) conv_fp32x_kernel(ConvArgs A, Tables T,
     const int chunk = item % n_chunks;
     const int grp = item / n_chunks;
     const int ncol = (A.mb_max + 1) * (A.ms_max + 1);
-    const int k_begin = grp * group;
-    const int k_end = min(ncol, k_begin + group);
+    const int k_hi = A.k_hi < 0 ? ncol : A.k_hi;
+    const int k_begin = A.k_lo + grp * group;
+    const int k_end = min(k_hi, k_begin + group);
     unsigned long long n_elem = 0, n_sum = 0;
     conv_fp32x_item<NT, CPT, TL>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum);
     flush_counters(A.counters, n_elem, n_sum);
@@ -25,7 +26,8 @@ static int launch_conv_fp32x_t(const ConvArgs &a, const Tables &t, void *stream,
     const int per_chunk = NT * CPT;
     const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
     const int ncol = (a.mb_max + 1) * (a.ms_max + 1);
-    const long long items = (long long)n_chunks * ((ncol + group - 1) / group);
+    const int nk = (a.k_hi < 0 ? ncol : a.k_hi) - a.k_lo;
+    const long long items = (long long)n_chunks * ((nk + group - 1) / group);
     if (items == 0) return 0;
     if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
     conv_fp32x_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group);

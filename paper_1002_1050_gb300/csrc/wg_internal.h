@@ -40,6 +40,7 @@ struct ConvArgs {
     const double *b;  // interleaved complex [l][mb]
     double *c_out;    // interleaved complex [mb][ms][j]
     unsigned long long *counters;
+    int k_lo = 0, k_hi = -1;  // chain columns k = ms (mb_max + 1) + mb in [k_lo, k_hi); k_hi < 0: all
 };
 
 struct DTableBwdArgs {

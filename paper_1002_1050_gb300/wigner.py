@@ -13,6 +13,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -55,6 +56,7 @@ def load():
                 "wigner_d_table": [I, I, I, I, P, I, P, P, P],
                 "wigner_d_table_backward": [I, I, I, I, P, P, P, P],
                 "wigner_conv_sum": [I, I, I, I, P, P, P, I, P, P, P],
+                "wigner_conv_sum_host": [I, I, I, I, P, P, P, I, P, P],
                 "wigner_conv_sum_backward": [I, I, I, I, P, P, P, P, P, P, P, P, I, P],
                 "wigner_conv_sum_batched": [I, P, P],
                 "wigner_batch_plan_create": [P, I, P, I, P],
@@ -182,6 +184,45 @@ def wigner_conv_sum(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, form="
     with torch.cuda.device(beta.device):
         _check(lib.wigner_conv_sum(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
                                    _ptr(out), _ptr(counters), _stream(stream)))
+    return out
+
+
+def _host_tensor(x, dtype, name):
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(x)
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a numpy array or a CPU torch.Tensor")
+    if x.is_cuda:
+        raise ValueError(f"{name} must be in host memory (use wigner_conv_sum for device tensors)")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return x
+
+
+def wigner_conv_sum_host(beta, a, b, form="fp64", out=None, stream=None, sync=True):
+    """wigner_conv_sum on host buffers (numpy arrays or CPU tensors; pinned memory lets the
+    copies overlap the computation).  Returns out, a CPU complex128 tensor
+    (mb_max+1, ms_max+1, n_beta); with sync=False the caller synchronises the stream
+    before reading it."""
+    lib = load()
+    beta = _host_tensor(beta, torch.float64, "beta")
+    a = _host_tensor(a, torch.complex128, "a")
+    b = _host_tensor(b, torch.complex128, "b")
+    if a.dim() != 2 or b.dim() != 2 or beta.dim() != 1 or a.shape[0] != b.shape[0]:
+        raise ValueError("expected beta (n_beta,), a (l_max+1, ms_max+1), b (l_max+1, mb_max+1)")
+    l_max, ms_max, mb_max, nb = a.shape[0] - 1, a.shape[1] - 1, b.shape[1] - 1, beta.numel()
+    if out is None:
+        out = torch.empty((mb_max + 1, ms_max + 1, nb), dtype=torch.complex128, pin_memory=torch.cuda.is_available())
+    out = _host_tensor(out, torch.complex128, "out")
+    if tuple(out.shape) != (mb_max + 1, ms_max + 1, nb):
+        raise ValueError("out has the wrong shape")
+    s = _stream(stream)
+    _check(lib.wigner_conv_sum_host(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
+                                    _ptr(out), s))
+    if sync:
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
     return out
 
 
@@ -348,4 +389,4 @@ def exported_symbols():
             "wigner_batch_plan_destroy", "wigner_device_status", "wigner_error_string",
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
             "wigner_conv_sum_noalloc", "wigner_batch_plan_info", "wigner_plan_create", "wigner_plan_destroy",
-            "wigner_last_error"]
+            "wigner_last_error", "wigner_conv_sum_host"]

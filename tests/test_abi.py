@@ -86,3 +86,11 @@ def test_plan_and_last_error_validation(lib):
     assert lib.wigner_plan_create(ctypes.byref(h), ctypes.byref(prm)) == -1
     assert not h.value
     lib.wigner_plan_destroy(None)  # NULL is accepted
+
+
+def test_host_entry_point_validation(lib):
+    H = ctypes.c_void_p(0x1000)  # never touched: validation fails first
+    assert lib.wigner_conv_sum_host(8, 2, 8, 4, None, H, H, 0, H, None) == -1
+    assert lib.wigner_conv_sum_host(8, 9, 8, 4, H, H, H, 0, H, None) == -1   # mb_max > l_max
+    assert lib.wigner_conv_sum_host(8, 2, 8, 4, H, H, H, 5, H, None) == -1   # unknown form
+    assert lib.wigner_conv_sum_host(8, 2, 8, 0, None, None, None, 0, None, None) == 0  # nothing to do
