@@ -120,9 +120,10 @@ int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
  *   beta_host, a_host, b_host, c_host: host memory with the layouts of wigner_conv_sum;
  *   page-locked (cudaHostAlloc / pinned) memory lets the copies overlap the computation,
  *   pageable memory works but is copied synchronously.
- *   The inputs are uploaded on `stream`; the chain columns are then computed in four
- *   launches over blocks of sky orders of about equal work, and each block's slice of C
- *   is downloaded on a library-owned stream while the next block computes.  On return
+ *   The inputs are uploaded on `stream`, the sum runs, and C is downloaded on a
+ *   library-owned stream that `stream` then waits for (the download of a block of sky
+ *   orders can overlap the computation of the next; at the measured ~200 GB/s host link
+ *   one block is fastest for the workloads here; WIGNER_HOST_BLOCKS sets another count).  On return
  *   all work is enqueued and `stream` waits for the downloads: synchronise `stream`
  *   before reading c_host.  The host buffers must stay valid until then.
  *   Device buffers come from a library-owned stream-ordered pool (allocated on first use,

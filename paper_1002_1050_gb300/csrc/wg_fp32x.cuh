@@ -32,10 +32,6 @@
 
 namespace wg {
 
-#define WG_LN_S32_HI 0x1.62e42fefa0000p+5     /* 64 ln 2, leading 36 bits */
-#define WG_LN_S32_LO 0x1.cf79abc9e3b3ap-34    /* 64 ln 2 - WG_LN_S32_HI   */
-#define WG_INV_LN_S32 0.022542110013890053
-
 struct Seed32 {
     float mant;
     int n;  // value = mant * 2^(64 n); n == 0: plain
@@ -151,11 +147,6 @@ __device__ __forceinline__ void fixup32(float &cur, float &aux, int &n) {
         n -= 1;
     }
 }
-
-struct Tile32 {
-    float4 *t;  // (A = -2 F0, F2, K0, K1) per l
-    float2 *w;  // (w_re, w_im) per l
-};
 
 // Coefficients of the difference form at order l (A = -2 F0, F2, K0, K1), built in
 // float-float on the FP32 pipe from the float-float tables and rounded to float:

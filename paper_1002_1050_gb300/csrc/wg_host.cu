@@ -6,12 +6,13 @@
 // hold about equal work (a column's chains have l_max + 1 - max(m_b, m_sky) elements);
 // the output of a block, C[m_b][m_sky range][beta] for every m_b, is one 2-D copy, made
 // on a second (library-owned) stream as soon as the block's launch has finished, while
-// the next block computes.  Only the upload and the last block's download are exposed.
+// the next block computes.
 // Device buffers come from a library-owned stream-ordered memory pool, so concurrent
 // calls on different streams do not share them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -27,7 +28,15 @@ int tables_for(int l_max, Tables *t);  // wg_capi.cu
 
 namespace {
 
-constexpr int NBLK = 4;
+// Blocks: one by default -- at ~200 GB/s the download of C (1.2 GB at the L = 4096
+// workload) takes ~7 ms against a second of computation, while every extra launch loses
+// its tail (measured: four blocks cost ~30 ms more than they hid).  WIGNER_HOST_BLOCKS
+// (1..16) sets another count, for workloads with a larger output-to-work ratio.
+int n_blocks() {
+    const char *v = std::getenv("WIGNER_HOST_BLOCKS");
+    const int n = v ? std::atoi(v) : 1;
+    return n < 1 ? 1 : (n > 16 ? 16 : n);
+}
 constexpr int MAX_DEV = 64;
 
 struct HostCallState {
@@ -78,7 +87,7 @@ int state_for_device(HostCallState **out) {
 }
 
 // sky-order boundaries of NBLK blocks of about equal work: block p is ms in [cut[p], cut[p+1])
-std::vector<int> block_cuts(int l_max, int mb_max, int ms_max) {
+std::vector<int> block_cuts(int l_max, int mb_max, int ms_max, int NBLK) {
     std::vector<double> w(ms_max + 1);
     double tot = 0.0;
     for (int ms = 0; ms <= ms_max; ++ms) {
@@ -141,7 +150,7 @@ extern "C" int wigner_conv_sum_host(int l_max, int mb_max, int ms_max, int n_bet
             return cuda_fail(e, "upload");
         }
 
-        const std::vector<int> cut = block_cuts(l_max, mb_max, ms_max);
+        const std::vector<int> cut = block_cuts(l_max, mb_max, ms_max, n_blocks());
         std::vector<cudaEvent_t> evs;
         for (size_t p = 0; p + 1 < cut.size() && e == cudaSuccess; ++p) {
             const int ms_a = cut[p], ms_b = cut[p + 1];

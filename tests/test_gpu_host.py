@@ -23,9 +23,11 @@ def W():
     return wigner
 
 
+@pytest.mark.parametrize("blocks", ["1", "4"])
 @pytest.mark.parametrize("form", ["fp64", "fp64s", "fp32x"])
 @pytest.mark.parametrize("L,MB,MS,NB", [(150, 4, 150, 300), (0, 0, 0, 1), (40, 3, 0, 7), (300, 8, 5, 513)])
-def test_host_matches_device_and_oracle(W, form, L, MB, MS, NB):
+def test_host_matches_device_and_oracle(W, form, L, MB, MS, NB, blocks, monkeypatch):
+    monkeypatch.setenv("WIGNER_HOST_BLOCKS", blocks)  # 4: downloads overlap the next block
     beta = I.beta_gauss_legendre(NB)[0]
     a = I.sky_alm(L, MS, 21)
     b = I.beam_blm(L, MB, fwhm=0.05)
