@@ -38,10 +38,15 @@
  *     carried normalised by a product of the F2 coefficients) and the weighted sum in
  *     float-float (~48-bit) arithmetic on the FP32 pipe; its C agrees with WG_FP64 to
  *     ~1e-13 (fused sums only; the d-table and adjoints treat it as WG_FP64).
- *     WG_FP32X runs the recursion body in float with an int32 exponent carry (a
- *     difference form of the recursion that keeps float accuracy at the poles and
- *     turning points) and compensated float sums, with double for the seeds and the
- *     coefficient tables; its error is stated per workload.
+ *     WG_FP32X runs the recursion body in float with an int32 exponent carry: away
+ *     from the poles (sin beta >= max(0.1, 1.2e-5 l_max)) the chain normalised by a
+ *     product of the F2 coefficients (two FMAs per step), near the poles a difference
+ *     form of the recursion that keeps float accuracy there; seeds and coefficients in
+ *     float-float, compensated float sums.  Its error is stated per workload (relative
+ *     L2 ~4e-6 on C at l_max = 8192; tests bind 2e-4 on d and 1e-4 on C).
+ *   - No kernel waits on another CTA or a flag.  The FP64 fused sums stage their
+ *     weights by TMA and wait on an mbarrier with a bounded number of tries; a wait
+ *     that gives up records WG_ERR_TIMEOUT in the device status word.
  */
 #ifndef WIGNER_GB300_H
 #define WIGNER_GB300_H
@@ -121,11 +126,12 @@ int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
  *   page-locked (cudaHostAlloc / pinned) memory lets the copies overlap the computation,
  *   pageable memory works but is copied synchronously.
  *   The inputs are uploaded on `stream`, the sum runs, and C is downloaded on a
- *   library-owned stream that `stream` then waits for (the download of a block of sky
- *   orders can overlap the computation of the next; at the measured ~200 GB/s host link
- *   one block is fastest for the workloads here; WIGNER_HOST_BLOCKS sets another count).  On return
- *   all work is enqueued and `stream` waits for the downloads: synchronise `stream`
- *   before reading c_host.  The host buffers must stay valid until then.
+ *   library-owned stream that `stream` then waits for.  The columns can be computed in
+ *   blocks of sky orders whose downloads overlap the next block's computation; at the
+ *   measured ~200 GB/s host link one block is fastest for the workloads here, and the
+ *   environment variable WIGNER_HOST_BLOCKS (1..16) sets another count.  On return all
+ *   work is enqueued and `stream` waits for the downloads: synchronise `stream` before
+ *   reading c_host.  The host buffers must stay valid until then.
  *   Device buffers come from a library-owned stream-ordered pool (allocated on first use,
  *   kept for later calls), so calls on different streams may run concurrently.
  *   Errors: as wigner_conv_sum (NULL host buffers: WG_ERR_ARG; no room: WG_ERR_ALLOC).
