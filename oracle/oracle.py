@@ -59,6 +59,8 @@ def _open(path):
     lib.oracle_d_single.restype = ctypes.c_double
     lib.oracle_conv_sum.argtypes = [I, I, I, I, P, P, P, P]
     lib.oracle_conv_sum.restype = I
+    lib.oracle_conv_sum_full.argtypes = [I, I, I, I, P, P, P, P]
+    lib.oracle_conv_sum_full.restype = I
     lib.oracle_conv_sum_sampled.argtypes = [I, I, I, I, P, P, P, I, P, P]
     lib.oracle_conv_sum_sampled.restype = I
     lib.oracle_conv_grad.argtypes = [I, I, I, I, P, P, P, P, P, P, P]
@@ -90,6 +92,9 @@ class Planted:
 
     def d_single(self, *args, **kw):
         return d_single(*args, _lib=self._lib, **kw)
+
+    def conv_sum_full(self, *args, **kw):
+        return conv_sum_full(*args, _lib=self._lib, **kw)
 
 
 def _ptr(x):
@@ -139,6 +144,19 @@ def conv_sum(l_max: int, mb_max: int, ms_max: int, beta, a, b, _lib=None) -> np.
     rc = lib.oracle_conv_sum(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b), _ptr(out))
     if rc != 0:
         raise ValueError("oracle_conv_sum: invalid arguments")
+    return out
+
+
+def conv_sum_full(l_max: int, mb_max: int, ms_max: int, beta, a, b, _lib=None) -> np.ndarray:
+    """C[mb][ms + ms_max][j] for every sky order -ms_max <= ms <= ms_max of a real sky
+    (s_{l,-m} = (-1)^m conj(a[l][m])); each negative order runs its own chain."""
+    lib = _lib or _load()
+    beta, a, b = _f64(beta), _c128(a), _c128(b)
+    assert a.shape == (l_max + 1, ms_max + 1) and b.shape == (l_max + 1, mb_max + 1)
+    out = np.empty((mb_max + 1, 2 * ms_max + 1, beta.size), dtype=np.complex128)
+    rc = lib.oracle_conv_sum_full(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_conv_sum_full: invalid arguments")
     return out
 
 

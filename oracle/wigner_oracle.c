@@ -74,22 +74,36 @@ static angle_t make_angle(double beta) {
 
 static ldbl ln_fact(int n) { return lgammal((ldbl)n + 1.0L); }
 
-/* ---- seed: d^{l0}_{mb,ms}(beta), l0 = max(mb, ms)  (Eqs. ini1-ini2, logstart) ----
- * ms >= mb : d^{l0}_{mb, l0} = A c^{l0+mb} s^{l0-mb},        A = sqrt((2l0)!/((l0+mb)!(l0-mb)!))
- * mb >  ms : d^{l0}_{l0, ms} = A c^{l0+ms} (-s)^{l0-ms},     A = sqrt((2l0)!/((l0+ms)!(l0-ms)!))
+/* ---- seed: d^{l0}_{m,mp}(beta), l0 = max(|m|, |mp|)  (Eqs. ini1-ini2, logstart) ----
+ * With c = cos(beta/2), s = sin(beta/2) the four edge values of Sec. 3.2 are
+ *   mp =  l0 (|m| <= l0): d^{l0}_{m, l0}  = A c^{l0+m}  s^{l0-m},     A = sqrt((2l0)!/((l0+m)!(l0-m)!))
+ *   mp = -l0 (|m| <= l0): d^{l0}_{m,-l0}  = A c^{l0-m}  (-s)^{l0+m}
+ *   m  =  l0 (|mp| < l0): d^{l0}_{l0, mp} = A c^{l0+mp} (-s)^{l0-mp}, A = sqrt((2l0)!/((l0+mp)!(l0-mp)!))
+ *   m  = -l0 (|mp| < l0): d^{l0}_{-l0,mp} = A c^{l0-mp} s^{l0+mp}
+ * (for m, mp >= 0 only the first and third occur).
  * Returns the scaled pair (mant, n): value = mant * 2^(90 n), mant in [1, 2^90) or 0.
  * pc, ps receive the exponents of c and s (for the derivative of the seed). */
-static void seed_scaled(int mb, int ms, const angle_t *t, double *mant, int *n, int *pc, int *ps) {
-    int l0 = mb > ms ? mb : ms;
-    int m = mb > ms ? ms : mb;
-    int p = l0 + m, q = l0 - m;
-    int sign = (mb > ms && (q & 1)) ? -1 : 1;
+static void seed_scaled(int m, int mp, const angle_t *t, double *mant, int *n, int *pc, int *ps) {
+    int am = m < 0 ? -m : m, amp = mp < 0 ? -mp : mp;
+    int l0 = am > amp ? am : amp;
+    int k;   /* the order that is not at the edge: A = sqrt((2l0)!/((l0+k)!(l0-k)!)) */
+    int p, q, neg_s;
+    if (amp >= am) {
+        k = m;
+        if (mp >= 0) { p = l0 + m; q = l0 - m; neg_s = 0; }
+        else         { p = l0 - m; q = l0 + m; neg_s = 1; }
+    } else {
+        k = mp;
+        if (m >= 0)  { p = l0 + mp; q = l0 - mp; neg_s = 1; }
+        else         { p = l0 - mp; q = l0 + mp; neg_s = 0; }
+    }
+    int sign = (neg_s && (q & 1)) ? -1 : 1;
 #if ORACLE_PLANT == 2
     sign = 1; /* planted: sign of (-sin(beta/2))^(l-m) dropped */
 #endif
     *pc = p;
     *ps = q;
-    ldbl r = 0.5L * (ln_fact(2 * l0) - ln_fact(l0 + m) - ln_fact(l0 - m));
+    ldbl r = 0.5L * (ln_fact(2 * l0) - ln_fact(l0 + k) - ln_fact(l0 - k));
     /* a zero power contributes nothing even where the logarithm is -inf */
     if (p > 0) {
         if (isinf(t->lnc)) { *mant = 0.0; *n = 0; return; } /* early stop: all values 0 (Sec. 3.2) */
@@ -104,10 +118,10 @@ static void seed_scaled(int mb, int ms, const angle_t *t, double *mant, int *n, 
 #endif
     }
     ldbl ln_s = (ldbl)ORACLE_LOG2_S * logl(2.0L);
-    ldbl k = floorl(r / ln_s);
-    ldbl rem = r - k * ln_s; /* in [0, ln S) up to rounding */
+    ldbl kk_ = floorl(r / ln_s);
+    ldbl rem = r - kk_ * ln_s; /* in [0, ln S) up to rounding */
     ldbl v = expl(rem);
-    int kk = (int)k;
+    int kk = (int)kk_;
     /* renormalise if rounding pushed v just outside [1, S) */
     if (v >= ldexpl(1.0L, ORACLE_LOG2_S)) { v = ldexpl(v, -ORACLE_LOG2_S); kk += 1; }
     if (v < 1.0L) { v = ldexpl(v, ORACLE_LOG2_S); kk -= 1; }
@@ -154,7 +168,8 @@ typedef struct {
 typedef void (*chain_visit)(void *ctx, int l, double mant, double dmant, int n);
 
 static void run_chain(const chain_spec *cs, chain_visit visit, void *ctx) {
-    int l0 = cs->mb > cs->ms ? cs->mb : cs->ms;
+    int amb = cs->mb < 0 ? -cs->mb : cs->mb, ams = cs->ms < 0 ? -cs->ms : cs->ms;
+    int l0 = amb > ams ? amb : ams;
     if (l0 > cs->l_max) return;
     double cur, prev = 0.0, dcur = 0.0, dprev = 0.0;
     int n, pc, ps;
@@ -262,7 +277,7 @@ int oracle_d_column(int l_max, int mb, int ms, int n_beta, const double *beta, d
     return 0;
 }
 
-/* Single element d^l_{m m'}(beta) for 0 <= m, m' <= l (used by sampled checks). */
+/* Single element d^l_{m m'}(beta) for |m|, |m'| <= l (used by sampled checks). */
 typedef struct { int want_l; double val; } one_ctx;
 
 static void one_visit(void *vctx, int l, double mant, double dmant, int n) {
@@ -272,7 +287,7 @@ static void one_visit(void *vctx, int l, double mant, double dmant, int n) {
 }
 
 double oracle_d_single(int l, int m, int mp, double beta) {
-    if (m < 0 || mp < 0 || m > l || mp > l) return NAN;
+    if (m < -l || mp < -l || m > l || mp > l) return NAN;
     angle_t t = make_angle(beta);
     chain_spec cs = {l, m, mp, &t, 1, 0};
     one_ctx ctx = {l, 0.0};
@@ -328,6 +343,59 @@ int oracle_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
             chain_spec cs = {l_max, mb, ms, &ang[j], 1, 0};
             sum_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0.0, 0.0};
             run_chain(&cs, sum_visit, &ctx);
+            double *o = c_out + 2 * ((size_t)c * n_beta + j);
+            o[0] = ctx.cre;
+            o[1] = ctx.cim;
+        }
+    }
+    free(ang);
+    return 0;
+}
+
+/* The sum over every sky order, -ms_max <= m_sky <= ms_max, for a real sky field:
+ * s_{l,-m} = (-1)^m conj(s_{l m}) (Sec. 4.2, the b/s symmetry relation), so only the
+ * m_sky >= 0 coefficients a[l][m] are passed.  Each negative order runs its own chain
+ * d^l_{m_b,m_sky}(beta), m_sky < 0, from the general seed above.
+ * C[mb][ms + ms_max][j], shape (mb_max+1, 2 ms_max+1, n_beta). */
+typedef struct {
+    const double *a, *b;
+    int ms_max1, mb_max1, mb, ms;  /* ms may be negative */
+    double cre, cim;
+} full_ctx;
+
+static void full_visit(void *vctx, int l, double mant, double dmant, int n) {
+    (void)dmant;
+    full_ctx *c = (full_ctx *)vctx;
+    int am = c->ms < 0 ? -c->ms : c->ms;
+    const double *al = c->a + 2 * ((size_t)l * c->ms_max1 + am);
+    double sre = al[0], sim = al[1];
+    if (c->ms < 0) {  /* (-1)^m conj(a_{l,|m|}) */
+        double sg = (am & 1) ? -1.0 : 1.0;
+        sre = sg * al[0];
+        sim = -sg * al[1];
+    }
+    const double *bl = c->b + 2 * ((size_t)l * c->mb_max1 + c->mb);
+    double wre = bl[0] * sre + bl[1] * sim;  /* conj(b) * s */
+    double wim = bl[0] * sim - bl[1] * sre;
+    double d = unscale(mant, n);
+    c->cre += wre * d;
+    c->cim += wim * d;
+}
+
+int oracle_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                         const double *a, const double *b, double *c_out) {
+    if (check_orders(l_max, mb_max, ms_max, n_beta)) return -1;
+    angle_t *ang = (angle_t *)malloc(sizeof(angle_t) * (n_beta ? n_beta : 1));
+    for (int j = 0; j < n_beta; ++j) ang[j] = make_angle(beta[j]);
+    int ns = 2 * ms_max + 1;
+    int ncol = (mb_max + 1) * ns;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < ncol; ++c) {
+        int mb = c / ns, ms = c % ns - ms_max;
+        for (int j = 0; j < n_beta; ++j) {
+            chain_spec cs = {l_max, mb, ms, &ang[j], 1, 0};
+            full_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0};
+            run_chain(&cs, full_visit, &ctx);
             double *o = c_out + 2 * ((size_t)c * n_beta + j);
             o[0] = ctx.cre;
             o[1] = ctx.cim;
