@@ -141,6 +141,48 @@ int wigner_conv_sum_host(int l_max, int mb_max, int ms_max, int n_beta, const do
                          void *stream);
 
 /* ---------------------------------------------------------------------------
+ * wigner_conv_sum_full -- the sum of Eq. convdef over EVERY sky order, -ms_max <= m_sky
+ * <= ms_max (the C_{m_b m_sky}(beta) of the conviqt data cube, Sec. 4.1 Eq. conviqt),
+ * for a real sky field, s_{l,-m} = (-1)^m conj(s_{l m}) (Sec. 4.2 symmetries), so a
+ * holds only m_sky >= 0 as in wigner_conv_sum.
+ *   The angle grid must be mirror-symmetric: beta[N-1-j] = pi - beta[j] (to ~10 ulp),
+ *   as Gauss-Legendre and equispaced grids are.  Each chain (m_b, m_sky >= 0) at
+ *   beta[j] then also yields the order -m_sky at pi - beta[j] by the appendix identity
+ *   d^l_{m,-m'}(pi - beta) = (-1)^{l+m} d^l_{m m'}(beta) (the corrected sign): a second
+ *   weighted sum over the same recursion (Sec. 4.2, "use of symmetries").  A grid that
+ *   is not mirror-symmetric makes the negative orders NaN and records WG_ERR_ARG in
+ *   the device status word.
+ *   c_out[mb][ms + ms_max][j], wg_c64, shape (mb_max+1, 2 ms_max+1, n_beta), overwritten;
+ *   C_{-m_b,-m_sky} = conj(C_{m_b m_sky}) gives the negative beam orders.
+ *   form: WG_FP64 or WG_FP64S (WG_FP32X: WG_ERR_UNSUPPORTED).  counters: optional (per
+ *   chain, as wigner_conv_sum).
+ * ------------------------------------------------------------------------- */
+int wigner_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                         const wg_c64 *a, const wg_c64 *b, wg_form form, wg_c64 *c_out,
+                         wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * wigner_data_cube -- the conviqt data cube of Sec. 4.1, Eq. conviqt:
+ *   cube[j][p][q] = sum_{m_b=-mb_max}^{mb_max} sum_{m_sky=-ms_max}^{ms_max}
+ *                   e^{-i m_b alpha_p} e^{-i m_sky gamma_q} C_{m_b m_sky}(beta_j),
+ *   alpha_p = 2 pi p / n_alpha, gamma_q = 2 pi q / n_gamma,
+ *   from c_full = the output of wigner_conv_sum_full (m_b >= 0; the negative beam orders
+ *   follow from C_{-m_b,-m_sky} = conj(C_{m_b m_sky}), Sec. 4.2).  For real sky and beam
+ *   fields the cube is real: float64, shape (n_beta, n_alpha, n_gamma), overwritten.
+ *   n_alpha >= 2 mb_max + 1 and n_gamma >= 2 ms_max + 1 (no aliasing); sizes with small
+ *   prime factors transform fastest.  A kernel of the library scatters C into the
+ *   Hermitian half spectrum (through the library's stream-ordered pool: n_beta n_alpha
+ *   (n_gamma/2+1) complex values of scratch); cuFFT (libcufft.so.12, loaded at the first
+ *   call; WG_ERR_UNSUPPORTED if it cannot be) runs the batched 2-D complex-to-real
+ *   transforms.  cuFFT plans are kept per (device, n_alpha, n_gamma, n_beta) for the
+ *   process, with the workspace cuFFT allocates for them.
+ *   Errors: WG_ERR_ARG (orders, sizes, NULL or misaligned pointers), WG_ERR_ALLOC,
+ *   WG_ERR_CUDA (launch or cuFFT failure), WG_ERR_UNSUPPORTED.
+ * ------------------------------------------------------------------------- */
+int wigner_data_cube(int mb_max, int ms_max, int n_beta, const wg_c64 *c_full, int n_alpha, int n_gamma,
+                     double *cube, void *stream);
+
+/* ---------------------------------------------------------------------------
  * wigner_conv_sum_backward -- adjoint of wigner_conv_sum for a real loss L, in
  * PyTorch's convention for complex tensors (grad = dL/dRe + i dL/dIm):
  *   grad_a[l][ms]  = sum_mb b[l][mb] S[l][mb][ms],      S = sum_j grad_c[mb][ms][j] d^l(beta_j)

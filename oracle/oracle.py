@@ -61,6 +61,8 @@ def _open(path):
     lib.oracle_conv_sum.restype = I
     lib.oracle_conv_sum_full.argtypes = [I, I, I, I, P, P, P, P]
     lib.oracle_conv_sum_full.restype = I
+    lib.oracle_conv_sum_full_sampled.argtypes = [I, I, I, I, P, P, P, I, P, P]
+    lib.oracle_conv_sum_full_sampled.restype = I
     lib.oracle_conv_sum_sampled.argtypes = [I, I, I, I, P, P, P, I, P, P]
     lib.oracle_conv_sum_sampled.restype = I
     lib.oracle_conv_grad.argtypes = [I, I, I, I, P, P, P, P, P, P, P]
@@ -157,6 +159,19 @@ def conv_sum_full(l_max: int, mb_max: int, ms_max: int, beta, a, b, _lib=None) -
     rc = lib.oracle_conv_sum_full(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b), _ptr(out))
     if rc != 0:
         raise ValueError("oracle_conv_sum_full: invalid arguments")
+    return out
+
+
+def conv_sum_full_sampled(l_max: int, mb_max: int, ms_max: int, beta, a, b, idx) -> np.ndarray:
+    """conv_sum_full at the (mb, ms, j) triples of idx (ms may be negative), complex128 [n]."""
+    lib = _load()
+    beta, a, b = _f64(beta), _c128(a), _c128(b)
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32).reshape(-1, 3))
+    out = np.empty(idx.shape[0], dtype=np.complex128)
+    rc = lib.oracle_conv_sum_full_sampled(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b),
+                                          idx.shape[0], _ptr(idx), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_conv_sum_full_sampled: invalid arguments")
     return out
 
 

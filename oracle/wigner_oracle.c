@@ -429,6 +429,29 @@ int oracle_conv_sum_sampled(int l_max, int mb_max, int ms_max, int n_beta, const
     return 0;
 }
 
+/* oracle_conv_sum_full at a list of (mb, ms, j) triples, -ms_max <= ms <= ms_max. */
+int oracle_conv_sum_full_sampled(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                                 const double *a, const double *b, int n_samples, const int *idx,
+                                 double *out) {
+    if (check_orders(l_max, mb_max, ms_max, n_beta)) return -1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int s = 0; s < n_samples; ++s) {
+        int mb = idx[3 * s], ms = idx[3 * s + 1], j = idx[3 * s + 2];
+        if (mb < 0 || mb > mb_max || ms < -ms_max || ms > ms_max || j < 0 || j >= n_beta) {
+            out[2 * s] = NAN;
+            out[2 * s + 1] = NAN;
+            continue;
+        }
+        angle_t t = make_angle(beta[j]);
+        chain_spec cs = {l_max, mb, ms, &t, 1, 0};
+        full_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0};
+        run_chain(&cs, full_visit, &ctx);
+        out[2 * s] = ctx.cre;
+        out[2 * s + 1] = ctx.cim;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* gradients of a real loss through C (PyTorch's convention for complex        */
 /* tensors: grad = dL/dRe + i dL/dIm).                                        */

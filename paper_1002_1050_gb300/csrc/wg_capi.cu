@@ -260,6 +260,7 @@ int wigner_device_status(void *stream) {
         if (h & WG_DEVERR_TIMEOUT) return fail(WG_ERR_TIMEOUT, "a bounded device wait gave up");
         if (h & WG_DEVERR_BOUNDS) return fail(WG_ERR_DEVICE, "a device-side bounds check failed");
         if (h & WG_DEVERR_BETA) return fail(WG_ERR_ARG, "an angle was outside [0, pi] (or interior required)");
+        if (h & WG_DEVERR_GRID) return fail(WG_ERR_ARG, "the angle grid is not mirror-symmetric (beta[N-1-j] != pi - beta[j])");
         return WG_OK;
     } catch (const std::bad_alloc &) {
         return fail(WG_ERR_ALLOC, "host allocation failed");
@@ -323,6 +324,28 @@ int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
         if (form == WG_FP64) return launch_rc(wg::launch_conv_fp64(ca, t, stream), "conv_fp64 launch");
         if (form == WG_FP64S) return launch_rc(wg::launch_conv_fp64s(ca, t, stream), "conv_fp64s launch");
         return launch_rc(wg::launch_conv_fp32x(ca, t, stream), "conv_fp32x launch");
+    } catch (const std::bad_alloc &) {
+        return fail(WG_ERR_ALLOC, "host allocation failed");
+    }
+}
+
+int wigner_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const double *beta, const wg_c64 *a,
+                         const wg_c64 *b, wg_form form, wg_c64 *c_out, wg_counter *counters, void *stream) {
+    try {
+        WG_TRY(check_orders(l_max, mb_max, ms_max, n_beta));
+        if (form == WG_FP32X) return fail(WG_ERR_UNSUPPORTED, "the sum over every sky order is FP64 / FP64S only");
+        if (form != WG_FP64 && form != WG_FP64S) return fail(WG_ERR_ARG, "unknown form");
+        if (n_beta == 0) return WG_OK;
+        WG_TRY(check_ptr(beta, 8, "beta"));
+        WG_TRY(check_ptr(a, 16, "a"));
+        WG_TRY(check_ptr(b, 16, "b"));
+        WG_TRY(check_ptr(c_out, 16, "c_out"));
+        if (counters && !aligned(counters, 8)) return fail(WG_ERR_ARG, "counters misaligned");
+        wg::Tables t;
+        WG_TRY(get_tables(l_max, &t));
+        wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b,
+                        (double *)c_out, counters};
+        return launch_rc(wg::launch_conv_fp64_full(ca, t, stream, form == WG_FP64S), "conv_fp64_full launch");
     } catch (const std::bad_alloc &) {
         return fail(WG_ERR_ALLOC, "host allocation failed");
     }

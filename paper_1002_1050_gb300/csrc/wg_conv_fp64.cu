@@ -6,7 +6,7 @@
 
 namespace wg {
 
-template <int NT, int CPT, int TL, bool SUM_FF>
+template <int NT, int CPT, int TL, bool SUM_FF, bool FULL>
 __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int n_chunks, int group,
                                                        const __grid_constant__ WeightMaps wm) {
     __shared__ SmemFp64<TL> sm;
@@ -26,11 +26,11 @@ __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int
     __syncthreads();
     unsigned ph[2] = {0u, 0u};
     unsigned long long n_elem = 0, n_sum = 0;
-    conv_fp64_item<NT, CPT, TL, SUM_FF, true>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum, &wm, &st, ph);
+    conv_fp64_item<NT, CPT, TL, SUM_FF, true, FULL>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum, &wm, &st, ph);
     flush_counters(A.counters, n_elem, n_sum);
 }
 
-template <int NT, int CPT, int TL, bool SUM_FF>
+template <int NT, int CPT, int TL, bool SUM_FF, bool FULL = false>
 static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, int group) {
     const int per_chunk = NT * CPT;
     const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
@@ -43,7 +43,8 @@ static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, 
     WeightMaps wm;
     const int e = encode_weight_maps(a.a, a.b, a.l_max, a.mb_max, a.ms_max, TL, &wm);
     if (e != 0) return e;
-    conv_fp64_kernel<NT, CPT, TL, SUM_FF><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group, wm);
+    conv_fp64_kernel<NT, CPT, TL, SUM_FF, FULL><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group,
+                                                                                                wm);
     return (int)cudaGetLastError();
 }
 
@@ -54,6 +55,13 @@ int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream) {
 // all-double form: the normalised two-FMA recursion with the sum in FP64 FMAs
 int launch_conv_fp64(const ConvArgs &a, const Tables &t, void *stream) {
     return launch_conv_fp64_t<256, 2, 128, false>(a, t, stream, 4);
+}
+
+// every sky order (-ms_max..ms_max) for a mirror-symmetric angle grid; a.c_out is
+// [mb][ms + ms_max][j]
+int launch_conv_fp64_full(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff) {
+    return sum_ff ? launch_conv_fp64_t<256, 2, 128, true, true>(a, t, stream, 4)
+                  : launch_conv_fp64_t<256, 2, 128, false, true>(a, t, stream, 4);
 }
 
 }  // namespace wg

@@ -53,6 +53,8 @@ struct SmemFp64 {
     double2 sA[TL];        // (F0', G')   (phase 1: (F0, G))
     double2 sWd[TL];       // w_l = conj(b) a (phase 1), then w_l sigma_l
     float4 sW[TL];         // w_l sigma_l as float-float (re hi, lo, im hi, lo)
+    double2 sWnd[TL];      // FULL: weights of the order -m_sky at pi - beta (then times sigma_l)
+    float4 sWn[TL];        // FULL: the same as float-float
     long long sT[TL];      // bit pattern of 1e-30 / sigma_l
     double sF2[TL];        // F2_l (phase 1)
     double sSig[TL + 1];   // sigma_{ts + i}
@@ -75,7 +77,13 @@ __device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
 // TMA: the weights arrive by TMA (wm, st; the mbarriers initialised by the caller, their
 // phases in ph), else by plain loads.  Returns false if a TMA wait gave up (the status
 // word then has WG_DEVERR_TIMEOUT and no copy is left in flight).
-template <int NT, int CPT, int TL, bool SUM_FF, bool TMA = false>
+// FULL: the sum over every sky order (the data cube of Sec. 4.1, m_sky from -ms_max to
+// ms_max) for a mirror-symmetric angle grid (beta_{N-1-j} = pi - beta_j).  The chain of
+// (m_b, m_sky) at beta_j also gives the order -m_sky at pi - beta_j through the
+// appendix identity d^l_{m,-m'}(pi - beta) = (-1)^{l+m} d^l_{m m'}(beta) (corrected
+// sign): a second weighted sum with w^-_l = conj(b_{l m_b}) s_{l,-m_sky} (-1)^{l+m_b},
+// s_{l,-m} = (-1)^m conj(s_{l m}) for a real sky.  c_out is then [m_b][m_sky + ms_max][j].
+template <int NT, int CPT, int TL, bool SUM_FF, bool TMA = false, bool FULL = false>
 __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
                                                  int k_end, SmemFp64<TL> &sm, unsigned long long &n_elem,
                                                  unsigned long long &n_sum, const WeightMaps *wm = nullptr,
@@ -100,8 +108,8 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
         const int ms = k / MB1, mb = k - ms * MB1;
         const int l0 = mb > ms ? mb : ms;
 
-        double u[CPT], up[CPT], cre[CPT], cim[CPT];
-        ff are[CPT], aim[CPT];
+        double u[CPT], up[CPT], cre[CPT], cim[CPT], nre[CPT], nim[CPT];
+        ff are[CPT], aim[CPT], bre[CPT], bim[CPT];
         int nsc[CPT], lsum[CPT];
         bool plain[CPT], summing[CPT];
 #pragma unroll
@@ -115,6 +123,8 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
             cim[c] = 0.0;
             are[c] = ff{0.f, 0.f};
             aim[c] = ff{0.f, 0.f};
+            nre[c] = nim[c] = 0.0;
+            bre[c] = bim[c] = ff{0.f, 0.f};
             summing[c] = false;
             lsum[c] = L + 1;
         }
@@ -155,7 +165,7 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
             for (int i = tid; i < TL; i += NT) {  // phase 1: F0, G, F2, w
                 const int l = ts + i;
                 double f0 = 0.0, g = 0.0, f2 = 0.0;
-                double2 w = make_double2(0.0, 0.0);
+                double2 w = make_double2(0.0, 0.0), wn = make_double2(0.0, 0.0);
                 if (l <= L) {
                     if (l < L) lrec_coefficients(l, mb, ms, T, f0, g, f2);
                     double2 av, bv;
@@ -167,10 +177,15 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
                         bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
                     }
                     w = make_double2(bv.x * av.x + bv.y * av.y, bv.x * av.y - bv.y * av.x);
+                    if (FULL) {  // (-1)^{l + m_b + m_sky} conj(b a)
+                        const double sg = ((l + mb + ms) & 1) ? -1.0 : 1.0;
+                        wn = make_double2(sg * (bv.x * av.x - bv.y * av.y), -sg * (bv.x * av.y + bv.y * av.x));
+                    }
                 }
                 sm.sA[i] = make_double2(f0, g);
                 sm.sF2[i] = f2;
                 sm.sWd[i] = w;
+                if (FULL) sm.sWnd[i] = wn;
             }
             __syncthreads();
             if (TMA && ts + 2 * TL <= L) {  // this buffer has been read: request the tile after next
@@ -216,6 +231,19 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
                 } else {
                     sm.sWd[i] = w;
                 }
+                if (FULL) {
+                    double2 wn = sm.sWnd[i];
+                    wn.x *= sg;
+                    wn.y *= sg;
+                    if (SUM_FF) {
+                        float4 wf;
+                        dbl_to_ff(wn.x, wf.x, wf.y);
+                        dbl_to_ff(wn.y, wf.z, wf.w);
+                        sm.sWn[i] = wf;
+                    } else {
+                        sm.sWnd[i] = wn;
+                    }
+                }
                 sm.sT[i] = __double_as_longlong(WG_EPS_SUM / sg);
             }
             __syncthreads();
@@ -236,20 +264,32 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
                 if (warp_sum) {
                     if (SUM_FF) {
                         const float4 w = sm.sW[i];
+                        float4 wn;
+                        if (FULL) wn = sm.sWn[i];
 #pragma unroll
                         for (int c = 0; c < CPT; ++c) {
                             ff uu = split_ff(u[c]);
                             if (!summing[c]) uu = ff{0.f, 0.f};
                             ff_mac(are[c], w.x, w.y, uu.hi, uu.lo);
                             ff_mac(aim[c], w.z, w.w, uu.hi, uu.lo);
+                            if (FULL) {
+                                ff_mac(bre[c], wn.x, wn.y, uu.hi, uu.lo);
+                                ff_mac(bim[c], wn.z, wn.w, uu.hi, uu.lo);
+                            }
                         }
                     } else {
                         const double2 w = sm.sWd[i];
+                        double2 wn;
+                        if (FULL) wn = sm.sWnd[i];
 #pragma unroll
                         for (int c = 0; c < CPT; ++c) {
                             const double um = summing[c] ? u[c] : 0.0;
                             cre[c] = fma(w.x, um, cre[c]);
                             cim[c] = fma(w.y, um, cim[c]);
+                            if (FULL) {
+                                nre[c] = fma(wn.x, um, nre[c]);
+                                nim[c] = fma(wn.y, um, nim[c]);
+                            }
                         }
                     }
                 }
@@ -265,7 +305,11 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
                 }
             }
         }
-        double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
+        // output columns: m_sky (and, FULL, -m_sky at the mirrored angle N-1-j)
+        const size_t NS = FULL ? (size_t)2 * A.ms_max + 1 : (size_t)A.ms_max + 1;
+        const size_t col = (size_t)mb * NS + (FULL ? (size_t)(A.ms_max + ms) : (size_t)ms);
+        double2 *out = reinterpret_cast<double2 *>(A.c_out) + col * NB;
+        double2 *outn = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * NS + (size_t)(A.ms_max - ms)) * NB;
 #pragma unroll
         for (int c = 0; c < CPT; ++c) {
             if (valid[c]) {
@@ -276,6 +320,19 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
                     im = (double)aim[c].hi + (double)aim[c].lo;
                 }
                 out[jj[c]] = ang[c].bad ? make_double2(nan, nan) : make_double2(re, im);
+                if (FULL && ms > 0) {
+                    double nr = nre[c], ni = nim[c];
+                    if (SUM_FF) {
+                        nr = (double)bre[c].hi + (double)bre[c].lo;
+                        ni = (double)bim[c].hi + (double)bim[c].lo;
+                    }
+                    // the mirrored angle must be pi - beta_j (to rounding): else NaN and a status bit
+                    const int jm = NB - 1 - jj[c];
+                    const double bm = A.beta[jm];
+                    const bool mirror_ok = fabs(bm + A.beta[jj[c]] - WG_PI_HI) <= 1e-14;
+                    if (!mirror_ok) raise_status(T.status, WG_DEVERR_GRID);
+                    outn[jm] = (ang[c].bad || !mirror_ok) ? make_double2(nan, nan) : make_double2(nr, ni);
+                }
                 n_elem += (unsigned long long)(L + 1 - l0);
                 n_sum += (unsigned long long)(L + 1 - min(lsum[c], L + 1));
             }

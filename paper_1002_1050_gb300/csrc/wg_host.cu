@@ -24,6 +24,7 @@
 namespace wg {
 void set_last_error(const std::string &msg, int code);
 int tables_for(int l_max, Tables *t);  // wg_capi.cu
+int host_pool(cudaMemPool_t *pool);
 }  // namespace wg
 
 namespace {
@@ -107,6 +108,15 @@ std::vector<int> block_cuts(int l_max, int mb_max, int ms_max, int NBLK) {
 }
 
 }  // namespace
+
+// the library's stream-ordered memory pool of the current device (also used by the
+// data cube's scratch spectrum)
+int wg::host_pool(cudaMemPool_t *pool) {
+    HostCallState *st = nullptr;
+    const int rc = state_for_device(&st);
+    if (rc == WG_OK) *pool = st->pool;
+    return rc;
+}
 
 extern "C" int wigner_conv_sum_host(int l_max, int mb_max, int ms_max, int n_beta, const double *beta_host,
                                     const wg_c64 *a_host, const wg_c64 *b_host, wg_form form, wg_c64 *c_host,

@@ -21,6 +21,7 @@
 #define WG_DEVERR_BETA 1
 #define WG_DEVERR_TIMEOUT 2
 #define WG_DEVERR_BOUNDS 4
+#define WG_DEVERR_GRID 8     /* a sum over every sky order met an angle grid that is not mirror-symmetric */
 
 namespace wg {
 
@@ -66,6 +67,7 @@ struct ConvBwdArgs {
 int launch_dtable_fp64(const DTableArgs &a, const Tables &t, void *stream);
 int launch_dtable_fp32x(const DTableArgs &a, const Tables &t, void *stream);
 int launch_conv_fp64(const ConvArgs &a, const Tables &t, void *stream);
+int launch_conv_fp64_full(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff);
 int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream);
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream);
 int launch_dtable_bwd(const DTableBwdArgs &a, const Tables &t, void *stream);

@@ -57,6 +57,8 @@ def load():
                 "wigner_d_table_backward": [I, I, I, I, P, P, P, P],
                 "wigner_conv_sum": [I, I, I, I, P, P, P, I, P, P, P],
                 "wigner_conv_sum_host": [I, I, I, I, P, P, P, I, P, P],
+                "wigner_conv_sum_full": [I, I, I, I, P, P, P, I, P, P, P],
+                "wigner_data_cube": [I, I, I, P, I, I, P, P],
                 "wigner_conv_sum_backward": [I, I, I, I, P, P, P, P, P, P, P, P, I, P],
                 "wigner_conv_sum_batched": [I, P, P],
                 "wigner_batch_plan_create": [P, I, P, I, P],
@@ -184,6 +186,65 @@ def wigner_conv_sum(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, form="
     with torch.cuda.device(beta.device):
         _check(lib.wigner_conv_sum(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
                                    _ptr(out), _ptr(counters), _stream(stream)))
+    return out
+
+
+def wigner_conv_sum_full(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, form="fp64",
+                         out: torch.Tensor | None = None, counters: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """C[mb][ms + ms_max][j] for every sky order -ms_max <= ms <= ms_max of a real sky
+    (a holds m_sky >= 0), on a mirror-symmetric angle grid (beta[N-1-j] = pi - beta[j])."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    a = _dev_tensor(a, torch.complex128, "a")
+    b = _dev_tensor(b, torch.complex128, "b")
+    l_max, mb_max, ms_max, nb = _conv_shapes(beta, a, b)
+    if out is None:
+        out = torch.empty((mb_max + 1, 2 * ms_max + 1, nb), dtype=torch.complex128, device=beta.device)
+    _dev_tensor(out, torch.complex128, "out")
+    if tuple(out.shape) != (mb_max + 1, 2 * ms_max + 1, nb):
+        raise ValueError("out has the wrong shape")
+    if counters is not None:
+        _dev_tensor(counters, torch.int64, "counters")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_conv_sum_full(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
+                                        _ptr(out), _ptr(counters), _stream(stream)))
+    return out
+
+
+def fft_size(n: int) -> int:
+    """Smallest integer >= n whose prime factors are 2, 3, 5 and 7 (fast FFT lengths)."""
+    m = max(1, n)
+    while True:
+        k = m
+        for p in (2, 3, 5, 7):
+            while k % p == 0:
+                k //= p
+        if k == 1:
+            return m
+        m += 1
+
+
+def wigner_data_cube(c_full: torch.Tensor, n_alpha: int | None = None, n_gamma: int | None = None,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """cube[j][p][q] = sum_{m_b, m_sky} e^{-i m_b alpha_p} e^{-i m_sky gamma_q} C_{m_b m_sky}(beta_j)
+    from c_full = wigner_conv_sum_full(...) (shape (mb_max+1, 2 ms_max+1, n_beta)); float64
+    (n_beta, n_alpha, n_gamma), by default the smallest fast sizes without aliasing."""
+    lib = load()
+    c_full = _dev_tensor(c_full, torch.complex128, "c_full")
+    if c_full.dim() != 3 or c_full.shape[1] % 2 != 1:
+        raise ValueError("c_full must have shape (mb_max+1, 2 ms_max+1, n_beta)")
+    mb_max, ms_max, nb = c_full.shape[0] - 1, (c_full.shape[1] - 1) // 2, c_full.shape[2]
+    n_alpha = fft_size(2 * mb_max + 1) if n_alpha is None else n_alpha
+    n_gamma = fft_size(2 * ms_max + 1) if n_gamma is None else n_gamma
+    if out is None:
+        out = torch.empty((nb, n_alpha, n_gamma), dtype=torch.float64, device=c_full.device)
+    _dev_tensor(out, torch.float64, "out")
+    if tuple(out.shape) != (nb, n_alpha, n_gamma):
+        raise ValueError("out has the wrong shape")
+    with torch.cuda.device(c_full.device):
+        _check(lib.wigner_data_cube(mb_max, ms_max, nb, _ptr(c_full), n_alpha, n_gamma, _ptr(out),
+                                    _stream(stream)))
     return out
 
 
@@ -389,4 +450,4 @@ def exported_symbols():
             "wigner_batch_plan_destroy", "wigner_device_status", "wigner_error_string",
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
             "wigner_conv_sum_noalloc", "wigner_batch_plan_info", "wigner_plan_create", "wigner_plan_destroy",
-            "wigner_last_error", "wigner_conv_sum_host"]
+            "wigner_last_error", "wigner_conv_sum_host", "wigner_conv_sum_full", "wigner_data_cube"]
