@@ -291,6 +291,9 @@ def run_ours(args):
     dtable = None
     if not args.skip_dtable:
         dtable = _dtable_block(W, dev, stream, args)
+    cube = None
+    if not args.skip_cube:
+        cube = _cube_block(W, dev, stream, args, mean_ms=total_ms / args.steps)
 
     if rank != 0:
         if dist is not None:
@@ -338,6 +341,7 @@ def run_ours(args):
         "fp32x": fp32x,
         "grad": grad,
         "dtable": dtable,
+        "cube": cube,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -462,6 +466,57 @@ def _dtable_block(W, dev, stream, args):
     del out, flush
     torch.cuda.empty_cache()
     return res
+
+
+def _cube_block(W, dev, stream, args, mean_ms):
+    """The conviqt data cube of the L=4096 workload: wigner_conv_sum_full over every sky
+    order (2048 Gauss-Legendre angles made exactly mirror-symmetric) and
+    wigner_data_cube (18 x 8232 points per angle); times per launch, the full sum's
+    evaluations per second (both signs of m_sky) against two half sums, and the cube's
+    bytes moved."""
+    import torch
+    from paper_1002_1050_gb300 import inputs as I
+
+    g = I.beta_gauss_legendre(N_BETA)[0]
+    h = N_BETA // 2
+    beta_h = g.copy()
+    beta_h[N_BETA - h:] = math.pi - g[:h][::-1]
+    if N_BETA % 2:
+        beta_h[h] = math.pi / 2
+    beta = torch.from_numpy(beta_h).to(dev)
+    a = torch.from_numpy(I.sky_alm(L_MAX, MS_MAX, 0)).to(dev)
+    b = torch.from_numpy(I.beam_blm(L_MAX, MB_MAX)).to(dev)
+    cf = torch.empty((MB_MAX + 1, 2 * MS_MAX + 1, N_BETA), dtype=torch.complex128, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_full = timed(lambda: W.wigner_conv_sum_full(beta, a, b, out=cf), 2)
+    W.check_device_status()
+    na, ng = W.fft_size(2 * MB_MAX + 1), W.fft_size(2 * MS_MAX + 1)
+    cube = torch.empty((N_BETA, na, ng), dtype=torch.float64, device=dev)
+    ms_cube = timed(lambda: W.wigner_data_cube(cf, na, ng, out=cube), 3)
+    W.check_device_status()
+    half = I.n_elements(L_MAX, MB_MAX, MS_MAX, N_BETA)
+    zero = I.n_elements(L_MAX, MB_MAX, 0, N_BETA)  # the m_sky = 0 columns are not doubled
+    elems = 2 * half - zero
+    nbytes = cf.numel() * 16 + 2 * N_BETA * na * (ng // 2 + 1) * 16 + cube.numel() * 8
+    del cf, cube
+    torch.cuda.empty_cache()
+    return {"workload": f"{WORKLOAD} over every sky order (-{MS_MAX}..{MS_MAX}), {N_BETA} mirror-symmetric GL angles",
+            "full_sum": {"ms_per_launch": ms_full, "evals_per_s": elems / (ms_full / 1e3),
+                         "vs_two_half_sums": 2 * mean_ms / ms_full},
+            "data_cube": {"shape": [N_BETA, na, ng], "ms_per_launch": ms_cube,
+                          "bytes_moved": nbytes, "gb_per_s": nbytes / (ms_cube / 1e3) / 1e9,
+                          "note": "C read, half spectrum written and read by cuFFT, cube written"}}
 
 
 def _fp32x_block(W, dev, stream, args):
@@ -619,6 +674,7 @@ def main(argv=None):
     p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
     p.add_argument("--skip-grad", action="store_true", help="skip the forward/adjoint timing")
     p.add_argument("--skip-dtable", action="store_true", help="skip the d-table timing")
+    p.add_argument("--skip-cube", action="store_true", help="skip the full-sum and data-cube timing")
     p.add_argument("--dtable-steps", type=int, default=20)
     p.add_argument("--fp64s-steps", type=int, default=5)
     p.add_argument("--fp32x-steps", type=int, default=3)
