@@ -188,6 +188,21 @@ def conv_sum_sampled(l_max: int, mb_max: int, ms_max: int, beta, a, b, idx) -> n
     return out
 
 
+def conv_sum_multi(l_max: int, mb_max: int, ms_max: int, beta, a, b, sum_cols: bool = False) -> np.ndarray:
+    """Eq. convdef for several weight columns (the polarised pairs of the footnote of Sec. 4.1,
+    or Monte-Carlo skies): column k is conv_sum with a[k] and b (one beam) or b[k].
+    Returns (n_col, mb+1, ms+1, n_beta), or with sum_cols the sum over the columns."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    cols = [conv_sum(l_max, mb_max, ms_max, beta, a[k], b if b.ndim == 2 else b[k]) for k in range(a.shape[0])]
+    if sum_cols:
+        out = np.zeros((mb_max + 1, ms_max + 1, np.size(beta)), dtype=np.complex128)
+        for c in cols:
+            out += c
+        return out
+    return np.array(cols).reshape(a.shape[0], mb_max + 1, ms_max + 1, np.size(beta))
+
+
 def conv_grad(l_max: int, mb_max: int, ms_max: int, beta, a, b, grad_c,
               want_a: bool = True, want_b: bool = True, want_beta: bool = True):
     """(grad_a, grad_b, grad_beta) of a real loss whose gradient w.r.t. C is grad_c."""

@@ -27,6 +27,8 @@ __all__ = [
     "beam_blm",
     "CONFIGS",
     "make_config",
+    "mc_skies",
+    "polarised_columns",
     "n_elements",
 ]
 
@@ -112,6 +114,29 @@ CONFIGS = {
     "conv_fp32x_l8192": dict(l_max=8192, mb_max=16, ms_max=8192, n_beta=8192, grid="gl", seed=0),
     "grad_l2048": dict(l_max=2048, mb_max=8, ms_max=2048, n_beta=1024, grid="uniform", seed=0, target_seed=1),
 }
+
+
+def mc_skies(l_max: int, ms_max: int, n: int, seed: int) -> np.ndarray:
+    """n independent skies (a Monte-Carlo batch sharing one beam): sky_alm with seeds
+    seed, seed + 1, ...; complex128 (n, l_max+1, ms_max+1)."""
+    return np.ascontiguousarray(np.stack([sky_alm(l_max, ms_max, seed + k) for k in range(n)]))
+
+
+def polarised_columns(l_max: int, mb_max: int, ms_max: int, seed: int):
+    """Three (sky, beam) pairs standing for (T, G, C) of a polarised convolution: skies with
+    the sky_alm spectrum at relative amplitudes 1, 0.1 and 0.02, the elliptical beam for T
+    and, for G and C, beams of the same profile carried mostly at beam order 2 (ellipticity
+    0.3 and 0.1, C with a quarter-turn phase).  Returns a (3, l_max+1, ms_max+1) and
+    b (3, l_max+1, mb_max+1), complex128."""
+    a = np.stack([sky_alm(l_max, ms_max, seed + k) * amp for k, amp in enumerate((1.0, 0.1, 0.02))])
+    bt = beam_blm(l_max, mb_max)
+    bg = beam_blm(l_max, mb_max, ellipticity=0.3)
+    bc = 1j * beam_blm(l_max, mb_max, ellipticity=0.1)
+    for bb in (bg, bc):
+        if mb_max >= 2:
+            bb[:, 0] *= 0.05  # mostly order 2: the spin-2 part of a polarised beam
+    b = np.stack([bt, bg, bc])
+    return np.ascontiguousarray(a), np.ascontiguousarray(b)
 
 
 def make_config(name: str, n_beta: int | None = None, beta_slice: slice | None = None):
