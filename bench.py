@@ -291,6 +291,9 @@ def run_ours(args):
     dtable = None
     if not args.skip_dtable:
         dtable = _dtable_block(W, dev, stream, args)
+    multi = None
+    if not args.skip_multi:
+        multi = _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms=total_ms / args.steps)
     cube = None
     if not args.skip_cube:
         cube = _cube_block(W, dev, stream, args, mean_ms=total_ms / args.steps)
@@ -341,6 +344,7 @@ def run_ours(args):
         "fp32x": fp32x,
         "grad": grad,
         "dtable": dtable,
+        "multi": multi,
         "cube": cube,
     }
     print(json.dumps(line), flush=True)
@@ -519,6 +523,47 @@ def _cube_block(W, dev, stream, args, mean_ms):
                           "note": "C read, half spectrum written and read by cuFFT, cube written"}}
 
 
+def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
+    """Several weight columns through one recursion on the L=4096 workload: four
+    Monte-Carlo skies with one beam (one pass, four outputs) and the polarised total of
+    three (sky, beam) pairs (one output).  Times per launch, column-evaluations per second,
+    the speed-up over one wigner_conv_sum per column, and FP64 throughput counted as the
+    headline's 5 flops per element plus 4 per summed element and column."""
+    import torch
+    from paper_1002_1050_gb300 import inputs as I
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    nb = beta.numel()
+    a4 = torch.from_numpy(I.mc_skies(L_MAX, MS_MAX, 4, 100)).to(dev)
+    out4 = torch.empty((4, MB_MAX + 1, MS_MAX + 1, nb), dtype=torch.complex128, device=dev)
+    ms_mc = timed(lambda: W.wigner_conv_sum_multi(beta, a4, b, out=out4), 2)
+    W.check_device_status()
+    del out4, a4
+    ap, bp = I.polarised_columns(L_MAX, MB_MAX, MS_MAX, 100)
+    ap, bp = torch.from_numpy(ap).to(dev), torch.from_numpy(bp).to(dev)
+    outp = torch.empty((MB_MAX + 1, MS_MAX + 1, nb), dtype=torch.complex128, device=dev)
+    ms_pol = timed(lambda: W.wigner_conv_sum_multi(beta, ap, bp, sum_cols=True, out=outp), 3)
+    W.check_device_status()
+    del outp
+    torch.cuda.empty_cache()
+    fl4 = 5 * n_elem + 4 * 4 * n_sum
+    return {"workload": f"{WORKLOAD}: 4 Monte-Carlo skies with one beam; polarised total of 3 pairs",
+            "monte_carlo_4": {"ms_per_launch": ms_mc, "column_evals_per_s": 4 * n_elem / (ms_mc / 1e3),
+                              "vs_separate_calls": 4 * mean_ms / ms_mc,
+                              "fp64_tflops": fl4 / (ms_mc / 1e3) / 1e12},
+            "polarised_total_3": {"ms_per_launch": ms_pol, "vs_separate_calls": 3 * mean_ms / ms_pol}}
+
+
 def _fp32x_block(W, dev, stream, args):
     """The FP32 form on the 8192/16/8192/8192-angle workload: throughput, error against the
     FP64 kernel (every 16th angle), and speed-up over the FP64 kernel on that same subset."""
@@ -674,6 +719,7 @@ def main(argv=None):
     p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
     p.add_argument("--skip-grad", action="store_true", help="skip the forward/adjoint timing")
     p.add_argument("--skip-dtable", action="store_true", help="skip the d-table timing")
+    p.add_argument("--skip-multi", action="store_true", help="skip the several-column timing")
     p.add_argument("--skip-cube", action="store_true", help="skip the full-sum and data-cube timing")
     p.add_argument("--dtable-steps", type=int, default=20)
     p.add_argument("--fp64s-steps", type=int, default=5)

@@ -183,6 +183,31 @@ int wigner_data_cube(int mb_max, int ms_max, int n_beta, const wg_c64 *c_full, i
                      double *cube, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * wigner_conv_sum_multi -- the sum of Eq. convdef for n_col weight columns at once:
+ *   c_out[k][mb][ms][j] = sum_l conj(b_k[l][mb]) a[k][l][ms] d^l_{mb,ms}(beta_j),  0 <= k < n_col.
+ *   Polarised convolution (the footnote of Sec. 4.1) adds the sums of the pairs
+ *   (b^T, s^T), (b^G, s^G), (b^C, s^C); a Monte-Carlo run convolves many skies with one
+ *   beam.  Every column needs the same d^l, so the recursion runs once per pass of up to
+ *   four columns: 2 + 2K FP64 FMAs per element and K columns (WG_FP64), against 4K for K
+ *   separate wigner_conv_sum calls.  The weights are read with plain loads.
+ *   a: wg_c64, shape (n_col, l_max+1, ms_max+1), 16-byte aligned.
+ *   b: wg_c64, shape (l_max+1, mb_max+1) if b_shared != 0 (one beam for every column),
+ *      else (n_col, l_max+1, mb_max+1); 16-byte aligned.
+ *   sum_cols = 0: c_out[k] holds column k, shape (n_col, mb_max+1, ms_max+1, n_beta);
+ *      ceil(n_col / 4) launches.
+ *   sum_cols != 0: c_out holds sum_k of the columns (the polarised total), shape
+ *      (mb_max+1, ms_max+1, n_beta); the weight sum_k conj(b_k) a_k is formed per l inside
+ *      the kernel, so this costs one column's work; one launch (n_col = 0 gives zeros).
+ *   c_out is overwritten.
+ *   form: WG_FP64 or WG_FP64S (WG_FP32X: WG_ERR_UNSUPPORTED).  counters: optional; the
+ *   element counts are those of one column (the chains are shared).
+ *   No allocation.  Errors: as wigner_conv_sum.
+ * ------------------------------------------------------------------------- */
+int wigner_conv_sum_multi(int l_max, int mb_max, int ms_max, int n_beta, int n_col, const double *beta,
+                          const wg_c64 *a, const wg_c64 *b, int b_shared, int sum_cols, wg_form form,
+                          wg_c64 *c_out, wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
  * wigner_conv_sum_backward -- adjoint of wigner_conv_sum for a real loss L, in
  * PyTorch's convention for complex tensors (grad = dL/dRe + i dL/dIm):
  *   grad_a[l][ms]  = sum_mb b[l][mb] S[l][mb][ms],      S = sum_j grad_c[mb][ms][j] d^l(beta_j)

@@ -58,6 +58,7 @@ def load():
                 "wigner_conv_sum": [I, I, I, I, P, P, P, I, P, P, P],
                 "wigner_conv_sum_host": [I, I, I, I, P, P, P, I, P, P],
                 "wigner_conv_sum_full": [I, I, I, I, P, P, P, I, P, P, P],
+                "wigner_conv_sum_multi": [I, I, I, I, I, P, P, P, I, I, I, P, P, P],
                 "wigner_data_cube": [I, I, I, P, I, I, P, P],
                 "wigner_conv_sum_backward": [I, I, I, I, P, P, P, P, P, P, P, P, I, P],
                 "wigner_conv_sum_batched": [I, P, P],
@@ -209,6 +210,43 @@ def wigner_conv_sum_full(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, f
     with torch.cuda.device(beta.device):
         _check(lib.wigner_conv_sum_full(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
                                         _ptr(out), _ptr(counters), _stream(stream)))
+    return out
+
+
+def wigner_conv_sum_multi(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, form="fp64",
+                          sum_cols: bool = False, out: torch.Tensor | None = None,
+                          counters: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """C[k][mb][ms][j] = sum_l conj(b_k[l][mb]) a[k][l][ms] d^l_{mb,ms}(beta_j) for n_col weight
+    columns (Monte-Carlo skies, polarised pairs), all from one pass of the chains.
+
+    a: (n_col, l_max+1, ms_max+1); b: (l_max+1, mb_max+1), shared by every column, or
+    (n_col, l_max+1, mb_max+1), one per column.  Returns (n_col, mb_max+1, ms_max+1, n_beta),
+    or with sum_cols the sum over k (the polarised total), (mb_max+1, ms_max+1, n_beta)."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    a = _dev_tensor(a, torch.complex128, "a")
+    b = _dev_tensor(b, torch.complex128, "b")
+    if a.dim() != 3:
+        raise ValueError("a must be 3-D: a[k][l][m_sky]")
+    n_col = a.shape[0]
+    shared = b.dim() == 2
+    if not shared and (b.dim() != 3 or b.shape[0] != n_col):
+        raise ValueError("b must be b[l][m_b] (shared) or b[k][l][m_b] with a's number of columns")
+    l_max, ms_max, mb_max, nb = a.shape[1] - 1, a.shape[2] - 1, b.shape[-1] - 1, beta.numel()
+    if b.shape[-2] != l_max + 1:
+        raise ValueError("a and b must have the same number of l rows")
+    shape = (mb_max + 1, ms_max + 1, nb) if sum_cols else (n_col, mb_max + 1, ms_max + 1, nb)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.complex128, device=beta.device)
+    _dev_tensor(out, torch.complex128, "out")
+    if tuple(out.shape) != shape:
+        raise ValueError("out has the wrong shape")
+    if counters is not None:
+        _dev_tensor(counters, torch.int64, "counters")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_conv_sum_multi(l_max, mb_max, ms_max, nb, n_col, _ptr(beta), _ptr(a), _ptr(b),
+                                         int(shared), int(bool(sum_cols)), _form(form), _ptr(out), _ptr(counters),
+                                         _stream(stream)))
     return out
 
 
@@ -450,4 +488,5 @@ def exported_symbols():
             "wigner_batch_plan_destroy", "wigner_device_status", "wigner_error_string",
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
             "wigner_conv_sum_noalloc", "wigner_batch_plan_info", "wigner_plan_create", "wigner_plan_destroy",
-            "wigner_last_error", "wigner_conv_sum_host", "wigner_conv_sum_full", "wigner_data_cube"]
+            "wigner_last_error", "wigner_conv_sum_host", "wigner_conv_sum_full", "wigner_data_cube",
+            "wigner_conv_sum_multi"]

@@ -94,3 +94,15 @@ def test_host_entry_point_validation(lib):
     assert lib.wigner_conv_sum_host(8, 9, 8, 4, H, H, H, 0, H, None) == -1   # mb_max > l_max
     assert lib.wigner_conv_sum_host(8, 2, 8, 4, H, H, H, 5, H, None) == -1   # unknown form
     assert lib.wigner_conv_sum_host(8, 2, 8, 0, None, None, None, 0, None, None) == 0  # nothing to do
+
+
+def test_multi_entry_point_validation(lib):
+    # (l_max, mb, ms, nb, n_col, beta, a, b, b_shared, sum_cols, form, c, counters, stream)
+    assert lib.wigner_conv_sum_multi(8, 9, 8, 4, 2, FAKE, FAKE, FAKE, 1, 0, 0, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_multi(8, 2, 8, 4, -1, FAKE, FAKE, FAKE, 1, 0, 0, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_multi(8, 2, 8, 4, 2, None, FAKE, FAKE, 1, 0, 0, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_multi(8, 2, 8, 4, 2, FAKE, P(0x1008), FAKE, 1, 0, 0, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_multi(8, 2, 8, 4, 2, FAKE, FAKE, FAKE, 1, 0, 1, FAKE, None, None) == -6  # FP32X
+    assert lib.wigner_conv_sum_multi(8, 2, 8, 4, 2, FAKE, FAKE, FAKE, 1, 0, 5, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_multi(8, 2, 8, 0, 2, None, None, None, 1, 0, 0, None, None, None) == 0
+    assert lib.wigner_conv_sum_multi(8, 2, 8, 4, 0, FAKE, None, None, 1, 0, 0, FAKE, None, None) == 0
