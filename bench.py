@@ -548,6 +548,8 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
     out4 = torch.empty((4, MB_MAX + 1, MS_MAX + 1, nb), dtype=torch.complex128, device=dev)
     ms_mc = timed(lambda: W.wigner_conv_sum_multi(beta, a4, b, out=out4), 2)
     W.check_device_status()
+    ms_mc_s = timed(lambda: W.wigner_conv_sum_multi(beta, a4, b, form="fp64s", out=out4), 2)
+    W.check_device_status()
     del out4, a4
     ap, bp = I.polarised_columns(L_MAX, MB_MAX, MS_MAX, 100)
     ap, bp = torch.from_numpy(ap).to(dev), torch.from_numpy(bp).to(dev)
@@ -561,6 +563,8 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
             "monte_carlo_4": {"ms_per_launch": ms_mc, "column_evals_per_s": 4 * n_elem / (ms_mc / 1e3),
                               "vs_separate_calls": 4 * mean_ms / ms_mc,
                               "fp64_tflops": fl4 / (ms_mc / 1e3) / 1e12},
+            "monte_carlo_4_fp64s": {"ms_per_launch": ms_mc_s, "column_evals_per_s": 4 * n_elem / (ms_mc_s / 1e3),
+                                    "vs_separate_fp64_calls": 4 * mean_ms / ms_mc_s},
             "polarised_total_3": {"ms_per_launch": ms_pol, "vs_separate_calls": 3 * mean_ms / ms_pol}}
 
 
