@@ -65,6 +65,15 @@ def _open(path):
     lib.oracle_conv_sum_full_sampled.restype = I
     lib.oracle_conv_sum_sampled.argtypes = [I, I, I, I, P, P, P, I, P, P]
     lib.oracle_conv_sum_sampled.restype = I
+    D = ctypes.c_double
+    lib.oracle_conv_sum_lmin.argtypes = [I, I, I, I, P, P, P, D, P]
+    lib.oracle_conv_sum_lmin.restype = I
+    lib.oracle_conv_sum_full_lmin.argtypes = [I, I, I, I, P, P, P, D, P]
+    lib.oracle_conv_sum_full_lmin.restype = I
+    lib.oracle_conv_sum_full_sampled_lmin.argtypes = [I, I, I, I, P, P, P, I, P, D, P]
+    lib.oracle_conv_sum_full_sampled_lmin.restype = I
+    lib.oracle_l_first.argtypes = [I, I, I, D, D]
+    lib.oracle_l_first.restype = I
     lib.oracle_conv_grad.argtypes = [I, I, I, I, P, P, P, P, P, P, P]
     lib.oracle_conv_grad.restype = I
     lib.oracle_num_threads.argtypes = []
@@ -97,6 +106,9 @@ class Planted:
 
     def conv_sum_full(self, *args, **kw):
         return conv_sum_full(*args, _lib=self._lib, **kw)
+
+    def l_first(self, *args, **kw):
+        return l_first(*args, _lib=self._lib, **kw)
 
 
 def _ptr(x):
@@ -137,39 +149,54 @@ def d_single(l: int, m: int, mp: int, beta: float, _lib=None) -> float:
     return float((_lib or _load()).oracle_d_single(l, m, mp, float(beta)))
 
 
-def conv_sum(l_max: int, mb_max: int, ms_max: int, beta, a, b, _lib=None) -> np.ndarray:
-    """C[mb][ms][j] = sum_l conj(b[l][mb]) a[l][ms] d^l_{mb ms}(beta_j), complex128."""
+def conv_sum(l_max: int, mb_max: int, ms_max: int, beta, a, b, _lib=None, offset=None) -> np.ndarray:
+    """C[mb][ms][j] = sum_l conj(b[l][mb]) a[l][ms] d^l_{mb ms}(beta_j), complex128.
+    offset: the sum starts at the l_min of Eq. lmin for that offset (None: no cut)."""
     lib = _lib or _load()
     beta, a, b = _f64(beta), _c128(a), _c128(b)
     assert a.shape == (l_max + 1, ms_max + 1) and b.shape == (l_max + 1, mb_max + 1)
     out = np.empty((mb_max + 1, ms_max + 1, beta.size), dtype=np.complex128)
-    rc = lib.oracle_conv_sum(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b), _ptr(out))
+    if offset is not None:
+        rc = lib.oracle_conv_sum_lmin(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b),
+                                      float(offset), _ptr(out))
+    else:
+        rc = lib.oracle_conv_sum(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b), _ptr(out))
     if rc != 0:
         raise ValueError("oracle_conv_sum: invalid arguments")
     return out
 
 
-def conv_sum_full(l_max: int, mb_max: int, ms_max: int, beta, a, b, _lib=None) -> np.ndarray:
+def conv_sum_full(l_max: int, mb_max: int, ms_max: int, beta, a, b, _lib=None, offset=None) -> np.ndarray:
     """C[mb][ms + ms_max][j] for every sky order -ms_max <= ms <= ms_max of a real sky
-    (s_{l,-m} = (-1)^m conj(a[l][m])); each negative order runs its own chain."""
+    (s_{l,-m} = (-1)^m conj(a[l][m])); each negative order runs its own chain.
+    offset: with the l_min cut of Eq. lmin (None: no cut)."""
     lib = _lib or _load()
     beta, a, b = _f64(beta), _c128(a), _c128(b)
     assert a.shape == (l_max + 1, ms_max + 1) and b.shape == (l_max + 1, mb_max + 1)
     out = np.empty((mb_max + 1, 2 * ms_max + 1, beta.size), dtype=np.complex128)
-    rc = lib.oracle_conv_sum_full(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b), _ptr(out))
+    if offset is not None:
+        rc = lib.oracle_conv_sum_full_lmin(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b),
+                                           float(offset), _ptr(out))
+    else:
+        rc = lib.oracle_conv_sum_full(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b),
+                                      _ptr(out))
     if rc != 0:
         raise ValueError("oracle_conv_sum_full: invalid arguments")
     return out
 
 
-def conv_sum_full_sampled(l_max: int, mb_max: int, ms_max: int, beta, a, b, idx) -> np.ndarray:
+def conv_sum_full_sampled(l_max: int, mb_max: int, ms_max: int, beta, a, b, idx, offset=None) -> np.ndarray:
     """conv_sum_full at the (mb, ms, j) triples of idx (ms may be negative), complex128 [n]."""
     lib = _load()
     beta, a, b = _f64(beta), _c128(a), _c128(b)
     idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32).reshape(-1, 3))
     out = np.empty(idx.shape[0], dtype=np.complex128)
-    rc = lib.oracle_conv_sum_full_sampled(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b),
-                                          idx.shape[0], _ptr(idx), _ptr(out))
+    if offset is not None:
+        rc = lib.oracle_conv_sum_full_sampled_lmin(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a),
+                                                   _ptr(b), idx.shape[0], _ptr(idx), float(offset), _ptr(out))
+    else:
+        rc = lib.oracle_conv_sum_full_sampled(l_max, mb_max, ms_max, beta.size, _ptr(beta), _ptr(a), _ptr(b),
+                                              idx.shape[0], _ptr(idx), _ptr(out))
     if rc != 0:
         raise ValueError("oracle_conv_sum_full_sampled: invalid arguments")
     return out
@@ -186,6 +213,12 @@ def conv_sum_sampled(l_max: int, mb_max: int, ms_max: int, beta, a, b, idx) -> n
     if rc != 0:
         raise ValueError("oracle_conv_sum_sampled: invalid arguments")
     return out
+
+
+def l_first(l_max: int, mb: int, mp: int, beta: float, offset: float, _lib=None) -> int:
+    """First l of the sum of chain (mb, mp, beta) under the l_min cut of Eq. lmin
+    (max(|mb|, |mp|) if nothing is cut, l_max + 1 if the whole chain is)."""
+    return int((_lib or _load()).oracle_l_first(l_max, mb, mp, float(beta), float(offset)))
 
 
 def conv_sum_multi(l_max: int, mb_max: int, ms_max: int, beta, a, b, sum_cols: bool = False) -> np.ndarray:

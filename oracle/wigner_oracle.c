@@ -296,6 +296,38 @@ double oracle_d_single(int l, int m, int mp, double beta) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* The l_min cut of Sec. 4.2.1 (Eq. lmin, its second, approximate line): in the */
+/* chain (m_b, m', beta) the terms with l below                                 */
+/*     l_min = (sqrt(m'^2 + m_b^2 - 2 m' m_b cos beta) - offset) / sin beta      */
+/* lie in the non-classical, exponentially small region (Eq. classiccond) and   */
+/* are left out of the sum; offset > 0 moves the cut away from the turning      */
+/* point.  At sin beta = 0 (beta = 0) d = delta_{m_b m'}: the chain is left out */
+/* unless m_b = m'.  Returns the first l of the sum: l0 = max(|m_b|, |m'|) when */
+/* nothing is cut, l_max + 1 when the whole chain is.  Double precision, no     */
+/* contraction (the compile flags say so), every operation rounded once.        */
+/* ------------------------------------------------------------------------- */
+static int l_first(int l_max, int l0, int mb, int mp, const angle_t *t, double offset) {
+    if (t->sinb == 0.0) return (mb == mp) ? l0 : l_max + 1;
+    double q = (double)mb * (double)mb + (double)mp * (double)mp;
+#if ORACLE_PLANT == 8
+    q = q + (2.0 * (double)mb * (double)mp) * t->cosb; /* planted: sign of the cos term */
+#else
+    q = q - (2.0 * (double)mb * (double)mp) * t->cosb;
+#endif
+    double x = (sqrt(q) - offset) / t->sinb;
+    if (!(x <= (double)l_max)) return l_max + 1;
+    if (x <= (double)l0) return l0;
+    return (int)ceil(x);
+}
+
+int oracle_l_first(int l_max, int mb, int mp, double beta, double offset) {
+    int amb = mb < 0 ? -mb : mb, amp = mp < 0 ? -mp : mp;
+    int l0 = amb > amp ? amb : amp;
+    angle_t t = make_angle(beta);
+    return l_first(l_max, l0, mb, mp, &t, offset);
+}
+
+/* ------------------------------------------------------------------------- */
 /* beam-convolution l-sum, Eq. convdef                                        */
 /* ------------------------------------------------------------------------- */
 typedef struct {
@@ -303,10 +335,12 @@ typedef struct {
     int ms_max1, mb_max1, mb, ms;
     double cre, cim;      /* C accumulator */
     double ere, eim;      /* sum of w * d/dbeta accumulator */
+    int lfirst;           /* terms with l < lfirst are left out (the l_min cut; 0 = none) */
 } sum_ctx;
 
 static void sum_visit(void *vctx, int l, double mant, double dmant, int n) {
     sum_ctx *c = (sum_ctx *)vctx;
+    if (l < c->lfirst) return;
     const double *al = c->a + 2 * ((size_t)l * c->ms_max1 + c->ms);
 #if ORACLE_PLANT == 7
     const double *bl = c->b + 2 * ((size_t)l * c->mb_max1 + (c->mb_max1 - 1 - c->mb)); /* planted: wrong beam column */
@@ -329,9 +363,10 @@ static void sum_visit(void *vctx, int l, double mant, double dmant, int n) {
     c->eim += wim * dd;
 }
 
-/* C[mb][ms][j] = sum_{l=max(mb,ms)}^{l_max} conj(b[l][mb]) a[l][ms] d^l_{mb ms}(beta_j). */
-int oracle_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
-                    const double *a, const double *b, double *c_out) {
+/* C[mb][ms][j] = sum_{l=max(mb,ms)}^{l_max} conj(b[l][mb]) a[l][ms] d^l_{mb ms}(beta_j);
+ * cut != 0: the sum starts at the l_min of Eq. lmin for that offset. */
+static int conv_sum_impl(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                         const double *a, const double *b, int cut, double offset, double *c_out) {
     if (check_orders(l_max, mb_max, ms_max, n_beta)) return -1;
     angle_t *ang = (angle_t *)malloc(sizeof(angle_t) * (n_beta ? n_beta : 1));
     for (int j = 0; j < n_beta; ++j) ang[j] = make_angle(beta[j]);
@@ -339,10 +374,12 @@ int oracle_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < ncol; ++c) {
         int mb = c / (ms_max + 1), ms = c % (ms_max + 1);
+        int l0 = mb > ms ? mb : ms;
         for (int j = 0; j < n_beta; ++j) {
             chain_spec cs = {l_max, mb, ms, &ang[j], 1, 0};
-            sum_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0.0, 0.0};
-            run_chain(&cs, sum_visit, &ctx);
+            sum_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0.0, 0.0, 0};
+            if (cut) ctx.lfirst = l_first(l_max, l0, mb, ms, &ang[j], offset);
+            if (ctx.lfirst <= l_max) run_chain(&cs, sum_visit, &ctx);
             double *o = c_out + 2 * ((size_t)c * n_beta + j);
             o[0] = ctx.cre;
             o[1] = ctx.cim;
@@ -350,6 +387,16 @@ int oracle_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
     }
     free(ang);
     return 0;
+}
+
+int oracle_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                    const double *a, const double *b, double *c_out) {
+    return conv_sum_impl(l_max, mb_max, ms_max, n_beta, beta, a, b, 0, 0.0, c_out);
+}
+
+int oracle_conv_sum_lmin(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                         const double *a, const double *b, double offset, double *c_out) {
+    return conv_sum_impl(l_max, mb_max, ms_max, n_beta, beta, a, b, 1, offset, c_out);
 }
 
 /* The sum over every sky order, -ms_max <= m_sky <= ms_max, for a real sky field:
@@ -361,11 +408,13 @@ typedef struct {
     const double *a, *b;
     int ms_max1, mb_max1, mb, ms;  /* ms may be negative */
     double cre, cim;
+    int lfirst;                    /* as in sum_ctx */
 } full_ctx;
 
 static void full_visit(void *vctx, int l, double mant, double dmant, int n) {
     (void)dmant;
     full_ctx *c = (full_ctx *)vctx;
+    if (l < c->lfirst) return;
     int am = c->ms < 0 ? -c->ms : c->ms;
     const double *al = c->a + 2 * ((size_t)l * c->ms_max1 + am);
     double sre = al[0], sim = al[1];
@@ -382,8 +431,8 @@ static void full_visit(void *vctx, int l, double mant, double dmant, int n) {
     c->cim += wim * d;
 }
 
-int oracle_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
-                         const double *a, const double *b, double *c_out) {
+static int conv_sum_full_impl(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                              const double *a, const double *b, int cut, double offset, double *c_out) {
     if (check_orders(l_max, mb_max, ms_max, n_beta)) return -1;
     angle_t *ang = (angle_t *)malloc(sizeof(angle_t) * (n_beta ? n_beta : 1));
     for (int j = 0; j < n_beta; ++j) ang[j] = make_angle(beta[j]);
@@ -392,10 +441,12 @@ int oracle_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const do
 #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < ncol; ++c) {
         int mb = c / ns, ms = c % ns - ms_max;
+        int ams = ms < 0 ? -ms : ms, l0 = mb > ams ? mb : ams;
         for (int j = 0; j < n_beta; ++j) {
             chain_spec cs = {l_max, mb, ms, &ang[j], 1, 0};
-            full_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0};
-            run_chain(&cs, full_visit, &ctx);
+            full_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0};
+            if (cut) ctx.lfirst = l_first(l_max, l0, mb, ms, &ang[j], offset);
+            if (ctx.lfirst <= l_max) run_chain(&cs, full_visit, &ctx);
             double *o = c_out + 2 * ((size_t)c * n_beta + j);
             o[0] = ctx.cre;
             o[1] = ctx.cim;
@@ -403,6 +454,16 @@ int oracle_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const do
     }
     free(ang);
     return 0;
+}
+
+int oracle_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                         const double *a, const double *b, double *c_out) {
+    return conv_sum_full_impl(l_max, mb_max, ms_max, n_beta, beta, a, b, 0, 0.0, c_out);
+}
+
+int oracle_conv_sum_full_lmin(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                              const double *a, const double *b, double offset, double *c_out) {
+    return conv_sum_full_impl(l_max, mb_max, ms_max, n_beta, beta, a, b, 1, offset, c_out);
 }
 
 /* Same sum restricted to a list of (mb, ms, j) triples (sampled checks at full size).
@@ -421,7 +482,7 @@ int oracle_conv_sum_sampled(int l_max, int mb_max, int ms_max, int n_beta, const
         }
         angle_t t = make_angle(beta[j]);
         chain_spec cs = {l_max, mb, ms, &t, 1, 0};
-        sum_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0.0, 0.0};
+        sum_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0.0, 0.0, 0};
         run_chain(&cs, sum_visit, &ctx);
         out[2 * s] = ctx.cre;
         out[2 * s + 1] = ctx.cim;
@@ -429,10 +490,11 @@ int oracle_conv_sum_sampled(int l_max, int mb_max, int ms_max, int n_beta, const
     return 0;
 }
 
-/* oracle_conv_sum_full at a list of (mb, ms, j) triples, -ms_max <= ms <= ms_max. */
-int oracle_conv_sum_full_sampled(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
-                                 const double *a, const double *b, int n_samples, const int *idx,
-                                 double *out) {
+/* oracle_conv_sum_full at a list of (mb, ms, j) triples, -ms_max <= ms <= ms_max;
+ * cut != 0: with the l_min cut of Eq. lmin for that offset. */
+static int full_sampled_impl(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                             const double *a, const double *b, int n_samples, const int *idx,
+                             int cut, double offset, double *out) {
     if (check_orders(l_max, mb_max, ms_max, n_beta)) return -1;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int s = 0; s < n_samples; ++s) {
@@ -444,12 +506,26 @@ int oracle_conv_sum_full_sampled(int l_max, int mb_max, int ms_max, int n_beta, 
         }
         angle_t t = make_angle(beta[j]);
         chain_spec cs = {l_max, mb, ms, &t, 1, 0};
-        full_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0};
-        run_chain(&cs, full_visit, &ctx);
+        full_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0};
+        int ams = ms < 0 ? -ms : ms, l0 = mb > ams ? mb : ams;
+        if (cut) ctx.lfirst = l_first(l_max, l0, mb, ms, &t, offset);
+        if (ctx.lfirst <= l_max) run_chain(&cs, full_visit, &ctx);
         out[2 * s] = ctx.cre;
         out[2 * s + 1] = ctx.cim;
     }
     return 0;
+}
+
+int oracle_conv_sum_full_sampled(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                                 const double *a, const double *b, int n_samples, const int *idx,
+                                 double *out) {
+    return full_sampled_impl(l_max, mb_max, ms_max, n_beta, beta, a, b, n_samples, idx, 0, 0.0, out);
+}
+
+int oracle_conv_sum_full_sampled_lmin(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                                      const double *a, const double *b, int n_samples, const int *idx,
+                                      double offset, double *out) {
+    return full_sampled_impl(l_max, mb_max, ms_max, n_beta, beta, a, b, n_samples, idx, 1, offset, out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -496,7 +572,7 @@ int oracle_conv_grad(int l_max, int mb_max, int ms_max, int n_beta, const double
             }
             if (grad_beta) {
                 chain_spec cs = {l_max, mb, ms, &ang[j], 1, 1};
-                sum_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0.0, 0.0};
+                sum_ctx ctx = {a, b, ms_max + 1, mb_max + 1, mb, ms, 0.0, 0.0, 0.0, 0.0, 0};
                 run_chain(&cs, sum_visit, &ctx);
                 /* Re(conj(G) * E) */
                 gb_cols[(size_t)c * n_beta + j] = g[2 * j] * ctx.ere + g[2 * j + 1] * ctx.eim;

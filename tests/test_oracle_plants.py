@@ -3,7 +3,8 @@
 Each plant (ORACLE_PLANT=k in oracle/wigner_oracle.c, built into a separate
 library on the CPU) is a plausible slip: a dropped d^{l-1} term, a lost seed
 sign, cos for sin in the seed, a coefficient one order off, a pair not
-rescaled jointly, an unconjugated beam, a wrong beam column.  The battery below
+rescaled jointly, an unconjugated beam, a wrong beam column, the wrong sign of the
+cos term in the l_min cut (Eq. lmin).  The battery below
 re-runs a compact version of the pins; the real oracle passes every check and
 every planted copy fails at least one.
 """
@@ -75,7 +76,17 @@ def _conv_gl_projection(orc):
     return True
 
 
-BATTERY = [_small_exact, _long_scaled_chain, _conv_beta_zero, _conv_gl_projection]
+def _lmin_turning_point(orc):
+    """The cut at offset 0 sits at the exact turning point of Eq. lmin's first line."""
+    for mb, ms, b in [(8, 1000, 1.0), (16, 1500, 0.9), (4, 700, 2.2)]:
+        q = ms * ms + mb * mb - 2.0 * ms * mb * math.cos(b)
+        l_tp = -0.5 + 0.5 * math.sqrt(1.0 + 4.0 * q / math.sin(b) ** 2)
+        if not 0.0 <= orc.l_first(100000, mb, ms, b, 0.0) - l_tp <= 1.5:
+            return False
+    return True
+
+
+BATTERY = [_small_exact, _long_scaled_chain, _conv_beta_zero, _conv_gl_projection, _lmin_turning_point]
 
 
 def test_real_oracle_passes_battery():
@@ -83,7 +94,7 @@ def test_real_oracle_passes_battery():
         assert chk(O), chk.__name__
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_planted_mistake_is_caught(plant):
     orc = O.Planted(plant)
     assert not all(chk(orc) for chk in BATTERY), f"plant {plant} slipped through every pin"
