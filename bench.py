@@ -291,6 +291,9 @@ def run_ours(args):
     dtable = None
     if not args.skip_dtable:
         dtable = _dtable_block(W, dev, stream, args)
+    lmin = None
+    if not args.skip_lmin:
+        lmin = _lmin_block(W, dev, stream, beta, a, b, out, mean_ms=total_ms / args.steps)
     multi = None
     if not args.skip_multi:
         multi = _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms=total_ms / args.steps)
@@ -344,6 +347,7 @@ def run_ours(args):
         "fp32x": fp32x,
         "grad": grad,
         "dtable": dtable,
+        "lmin": lmin,
         "multi": multi,
         "cube": cube,
     }
@@ -568,6 +572,50 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
             "polarised_total_3": {"ms_per_launch": ms_pol, "vs_separate_calls": 3 * mean_ms / ms_pol}}
 
 
+def _lmin_block(W, dev, stream, beta, a, b, out, mean_ms):
+    """The l_min cut of Eq. lmin on the L=4096 workload at the paper's offsets (l_max/20,
+    30, 15): time per launch, share of the nominal elements evaluated, and the residual
+    against the exact FP64 sum in the paper's statistics (mean, RMS, max, and RMS relative
+    to the RMS of C)."""
+    import torch
+    from paper_1002_1050_gb300 import inputs as I
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    nb = beta.numel()
+    W.wigner_conv_sum(beta, a, b, out=out)
+    ref = out.clone()
+    rms_ref = float(torch.sqrt(torch.mean(torch.abs(ref) ** 2)))
+    cut = torch.empty_like(ref)
+    nominal = I.n_elements(L_MAX, MB_MAX, MS_MAX, nb)
+    rows = []
+    for off in (L_MAX / 20, 30.0, 15.0):
+        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        W.wigner_conv_sum_lmin(beta, a, b, off, out=cut, counters=cnt)
+        W.check_device_status()
+        ms_off = timed(lambda: W.wigner_conv_sum_lmin(beta, a, b, off, out=cut), 2)
+        r = torch.view_as_real(cut - ref)
+        res = torch.abs(cut - ref)
+        rows.append({"offset": off, "ms_per_launch": ms_off, "speedup_vs_exact": mean_ms / ms_off,
+                     "elements_evaluated_frac": int(cnt[0]) / nominal,
+                     "resid_mean_re": float(r[..., 0].mean()), "resid_rms": float(torch.sqrt(torch.mean(res ** 2))),
+                     "resid_max": float(res.max()),
+                     "resid_rel": float(torch.sqrt(torch.mean(res ** 2))) / rms_ref})
+    del ref, cut
+    torch.cuda.empty_cache()
+    return {"workload": f"{WORKLOAD}, the l_min cut at three offsets; residuals against the exact sum",
+            "exact_ms_per_launch": mean_ms, "rows": rows}
+
+
 def _fp32x_block(W, dev, stream, args):
     """The FP32 form on the 8192/16/8192/8192-angle workload: throughput, error against the
     FP64 kernel (every 16th angle), and speed-up over the FP64 kernel on that same subset."""
@@ -723,6 +771,7 @@ def main(argv=None):
     p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
     p.add_argument("--skip-grad", action="store_true", help="skip the forward/adjoint timing")
     p.add_argument("--skip-dtable", action="store_true", help="skip the d-table timing")
+    p.add_argument("--skip-lmin", action="store_true", help="skip the l_min-cut timing")
     p.add_argument("--skip-multi", action="store_true", help="skip the several-column timing")
     p.add_argument("--skip-cube", action="store_true", help="skip the full-sum and data-cube timing")
     p.add_argument("--dtable-steps", type=int, default=20)

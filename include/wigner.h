@@ -183,6 +183,27 @@ int wigner_data_cube(int mb_max, int ms_max, int n_beta, const wg_c64 *c_full, i
                      double *cube, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * wigner_conv_sum_lmin -- the sum of Eq. convdef with the l_min cut of Sec. 4.2.1
+ * (Eq. lmin, its approximate line): each chain (m_b, m_sky, beta_j) sums from
+ *   l_min = (sqrt(m_sky^2 + m_b^2 - 2 m_sky m_b cos beta_j) - offset) / sin beta_j
+ * (and from the first |d| >= 1e-30, as wigner_conv_sum); the terms below lie in the
+ * non-classical region, so the error falls steeply as offset grows (offset >= m_b + m_sky
+ * cuts nothing).  At beta = 0 (d = delta) a chain with m_b != m_sky is cut whole.  Chains
+ * cut whole are not computed: a CTA whose chains are all cut skips the column, a warp
+ * whose chains are all cut skips its steps, and their C is 0.
+ *   full = 0: the layout and inputs of wigner_conv_sum; full != 0: of wigner_conv_sum_full
+ *   (every sky order on a mirror-symmetric grid; the mirrored chain has the same l_min).
+ *   offset: any value but NaN (WG_ERR_ARG); the paper uses offset >= l_max / 20.
+ *   l_min is computed in double with each operation rounded once; an angle whose l_min
+ *   lies within rounding of an integer may place the cut one order either way.
+ *   form: WG_FP64 or WG_FP64S (WG_FP32X: WG_ERR_UNSUPPORTED).  counters: [0] counts the
+ *   elements of the chains whose warp ran the recursion.  Errors: as wigner_conv_sum.
+ * ------------------------------------------------------------------------- */
+int wigner_conv_sum_lmin(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
+                         const wg_c64 *a, const wg_c64 *b, wg_form form, double offset, int full,
+                         wg_c64 *c_out, wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
  * wigner_conv_sum_multi -- the sum of Eq. convdef for n_col weight columns at once:
  *   c_out[k][mb][ms][j] = sum_l conj(b_k[l][mb]) a[k][l][ms] d^l_{mb,ms}(beta_j),  0 <= k < n_col.
  *   Polarised convolution (the footnote of Sec. 4.1) adds the sums of the pairs

@@ -351,6 +351,32 @@ int wigner_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const do
     }
 }
 
+int wigner_conv_sum_lmin(int l_max, int mb_max, int ms_max, int n_beta, const double *beta, const wg_c64 *a,
+                         const wg_c64 *b, wg_form form, double offset, int full, wg_c64 *c_out,
+                         wg_counter *counters, void *stream) {
+    try {
+        WG_TRY(check_orders(l_max, mb_max, ms_max, n_beta));
+        if (form == WG_FP32X) return fail(WG_ERR_UNSUPPORTED, "the l_min cut is FP64 / FP64S only");
+        if (form != WG_FP64 && form != WG_FP64S) return fail(WG_ERR_ARG, "unknown form");
+        if (offset != offset) return fail(WG_ERR_ARG, "offset is NaN");
+        if (n_beta == 0) return WG_OK;
+        WG_TRY(check_ptr(beta, 8, "beta"));
+        WG_TRY(check_ptr(a, 16, "a"));
+        WG_TRY(check_ptr(b, 16, "b"));
+        WG_TRY(check_ptr(c_out, 16, "c_out"));
+        if (counters && !aligned(counters, 8)) return fail(WG_ERR_ARG, "counters misaligned");
+        wg::Tables t;
+        WG_TRY(get_tables(l_max, &t));
+        wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b,
+                        (double *)c_out, counters};
+        ca.offset = offset;
+        return launch_rc(wg::launch_conv_fp64_lmin(ca, t, stream, form == WG_FP64S, full != 0),
+                         "conv_fp64_lmin launch");
+    } catch (const std::bad_alloc &) {
+        return fail(WG_ERR_ALLOC, "host allocation failed");
+    }
+}
+
 int wigner_conv_sum_backward(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
                              const wg_c64 *a, const wg_c64 *b, const wg_c64 *c_fwd, const wg_c64 *grad_c,
                              wg_c64 *grad_a, wg_c64 *grad_b, double *grad_beta, wg_form form, void *stream) {

@@ -143,6 +143,30 @@ __device__ __forceinline__ void ff_mac(ff &acc, float wh, float wl, float uh, fl
     acc.lo = __fsub_rn(lo, __fsub_rn(acc.hi, s));
 }
 
+// ff_mac on a (re, im) pair with the packed f32x2 instructions: the same rounding steps
+// lane by lane (a - b is written fma(b, -1, a), which rounds a - b once, and p - bb as
+// -(np + bb) with np = -p), so each lane equals ff_mac's result bit for bit, in 15
+// instructions instead of 28.  (hi, lo): the accumulators; (wh, wl): the weight pair;
+// (uh, ul): the value as float-float.
+__device__ __forceinline__ void ff_mac2(float2 &hi, float2 &lo, float2 wh, float2 wl, float uh, float ul) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 Uh = make_float2(uh, uh), Ul = make_float2(ul, ul), nUh = make_float2(-uh, -uh);
+    const float2 np = __fmul2_rn(wh, nUh);          // -p
+    float2 e = __ffma2_rn(wh, Uh, np);              // wh uh - p, exact
+    e = __ffma2_rn(wh, Ul, e);
+    e = __ffma2_rn(wl, Uh, e);
+    const float2 s = __ffma2_rn(np, m1, hi);        // hi + p
+    const float2 bb = __ffma2_rn(hi, m1, s);        // s - hi
+    const float2 t1 = __ffma2_rn(bb, m1, s);        // s - bb
+    const float2 t2 = __ffma2_rn(t1, m1, hi);       // hi - (s - bb)
+    const float2 q = __fadd2_rn(np, bb);            // -(p - bb)
+    const float2 err = __ffma2_rn(q, m1, t2);       // t2 + (p - bb)
+    const float2 l2 = __fadd2_rn(lo, __fadd2_rn(err, e));
+    const float2 h2 = __fadd2_rn(s, l2);
+    lo = __ffma2_rn(__ffma2_rn(s, m1, h2), m1, l2);  // l2 - (h2 - s)
+    hi = h2;
+}
+
 // ---------------------------------------------------------------------------
 // exponent-field helpers
 // ---------------------------------------------------------------------------

@@ -6,7 +6,7 @@
 
 namespace wg {
 
-template <int NT, int CPT, int TL, bool SUM_FF, bool FULL>
+template <int NT, int CPT, int TL, bool SUM_FF, bool FULL, bool LMIN>
 __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int n_chunks, int group,
                                                        const __grid_constant__ WeightMaps wm) {
     __shared__ SmemFp64<TL> sm;
@@ -26,11 +26,12 @@ __global__ void __launch_bounds__(NT) conv_fp64_kernel(ConvArgs A, Tables T, int
     __syncthreads();
     unsigned ph[2] = {0u, 0u};
     unsigned long long n_elem = 0, n_sum = 0;
-    conv_fp64_item<NT, CPT, TL, SUM_FF, true, FULL>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum, &wm, &st, ph);
+    conv_fp64_item<NT, CPT, TL, SUM_FF, true, FULL, LMIN>(A, T, chunk, k_begin, k_end, sm, n_elem, n_sum, &wm, &st,
+                                                         ph);
     flush_counters(A.counters, n_elem, n_sum);
 }
 
-template <int NT, int CPT, int TL, bool SUM_FF, bool FULL = false>
+template <int NT, int CPT, int TL, bool SUM_FF, bool FULL = false, bool LMIN = false>
 static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, int group) {
     const int per_chunk = NT * CPT;
     const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
@@ -43,8 +44,8 @@ static int launch_conv_fp64_t(const ConvArgs &a, const Tables &t, void *stream, 
     WeightMaps wm;
     const int e = encode_weight_maps(a.a, a.b, a.l_max, a.mb_max, a.ms_max, TL, &wm);
     if (e != 0) return e;
-    conv_fp64_kernel<NT, CPT, TL, SUM_FF, FULL><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group,
-                                                                                                wm);
+    conv_fp64_kernel<NT, CPT, TL, SUM_FF, FULL, LMIN>
+        <<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group, wm);
     return (int)cudaGetLastError();
 }
 
@@ -62,6 +63,15 @@ int launch_conv_fp64(const ConvArgs &a, const Tables &t, void *stream) {
 int launch_conv_fp64_full(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff) {
     return sum_ff ? launch_conv_fp64_t<256, 2, 128, true, true>(a, t, stream, 4)
                   : launch_conv_fp64_t<256, 2, 128, false, true>(a, t, stream, 4);
+}
+
+// with the l_min cut of Eq. lmin (a.offset); full: every sky order as above
+int launch_conv_fp64_lmin(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff, bool full) {
+    if (full)
+        return sum_ff ? launch_conv_fp64_t<256, 2, 128, true, true, true>(a, t, stream, 4)
+                      : launch_conv_fp64_t<256, 2, 128, false, true, true>(a, t, stream, 4);
+    return sum_ff ? launch_conv_fp64_t<256, 2, 128, true, false, true>(a, t, stream, 4)
+                  : launch_conv_fp64_t<256, 2, 128, false, false, true>(a, t, stream, 4);
 }
 
 }  // namespace wg

@@ -74,6 +74,23 @@ __device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
     lo = __double2float_rn(x - (double)hi);
 }
 
+// The l_min cut of Sec. 4.2.1 (Eq. lmin, its approximate line): the chain (m_b, m_sky,
+// beta) sums from l_min = (sqrt(q) - offset) / sin beta, q = m_sky^2 + m_b^2 -
+// 2 m_sky m_b cos beta; the terms below lie in the non-classical region.  At sin beta = 0
+// (beta = 0, d = delta) the chain is left out unless m_b = m_sky.  Returns the first l of
+// the sum, l0 (nothing cut) up to L + 1 (the whole chain cut).  Every operation is
+// rounded once, without contraction.  The chain's mirror (m_b, -m_sky, pi - beta) has
+// the same q and sin, so one value serves both halves of the sum over every sky order.
+__device__ __forceinline__ int lmin_first(int L, int l0, int mb, int ms, const Angle &t, double offset) {
+    if (t.sb == 0.0) return mb == ms ? l0 : L + 1;
+    const double q0 = __dadd_rn(__dmul_rn((double)mb, (double)mb), __dmul_rn((double)ms, (double)ms));
+    const double q = __dsub_rn(q0, __dmul_rn(__dmul_rn(__dmul_rn(2.0, (double)mb), (double)ms), t.cb));
+    const double x = __ddiv_rn(__dsub_rn(__dsqrt_rn(q), offset), t.sb);
+    if (!(x <= (double)L)) return L + 1;
+    if (x <= (double)l0) return l0;
+    return (int)ceil(x);
+}
+
 // TMA: the weights arrive by TMA (wm, st; the mbarriers initialised by the caller, their
 // phases in ph), else by plain loads.  Returns false if a TMA wait gave up (the status
 // word then has WG_DEVERR_TIMEOUT and no copy is left in flight).
@@ -83,7 +100,10 @@ __device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
 // appendix identity d^l_{m,-m'}(pi - beta) = (-1)^{l+m} d^l_{m m'}(beta) (corrected
 // sign): a second weighted sum with w^-_l = conj(b_{l m_b}) s_{l,-m_sky} (-1)^{l+m_b},
 // s_{l,-m} = (-1)^m conj(s_{l m}) for a real sky.  c_out is then [m_b][m_sky + ms_max][j].
-template <int NT, int CPT, int TL, bool SUM_FF, bool TMA = false, bool FULL = false>
+// LMIN: the sum of each chain starts at lmin_first (offset A.offset); a CTA whose chains
+// are all cut skips the column (no tables, no copies), a warp whose chains are all cut
+// skips its recursion steps, and a cut chain's C is 0.
+template <int NT, int CPT, int TL, bool SUM_FF, bool TMA = false, bool FULL = false, bool LMIN = false>
 __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &T, int chunk, int k_begin,
                                                  int k_end, SmemFp64<TL> &sm, unsigned long long &n_elem,
                                                  unsigned long long &n_sum, const WeightMaps *wm = nullptr,
@@ -98,7 +118,10 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
     Angle ang[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        jj[c] = chunk * NT * CPT + c * NT + tid;
+        // LMIN: a warp's chains are 32 x CPT consecutive angles, so that the chains the cut
+        // removes (an interval of angles per column) tend to fill whole warps
+        jj[c] = LMIN ? chunk * NT * CPT + (tid >> 5) * (32 * CPT) + c * 32 + (tid & 31)
+                     : chunk * NT * CPT + c * NT + tid;
         valid[c] = jj[c] < NB;
         ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
         if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
@@ -128,10 +151,22 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
             summing[c] = false;
             lsum[c] = L + 1;
         }
+        int lfirst[CPT];
+        bool cta_live = true, warp_live = true;
+        if (LMIN) {
+            bool live = false;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                lfirst[c] = lmin_first(L, l0, mb, ms, ang[c], A.offset);
+                live |= valid[c] && lfirst[c] <= L;
+            }
+            cta_live = __syncthreads_or(live);
+            warp_live = __any_sync(0xffffffffu, live);
+        }
         bool warp_sum = false;
         double sig_m1 = 0.0, sig_0 = 1.0;  // thread 0's carry: sigma_{ts-1}, sigma_{ts}
         bool inflight[2] = {false, false};  // TMA: a tile requested and not yet waited for
-        if (TMA) {
+        if (TMA && cta_live) {
             if (tid == 0) {
                 tma_weights<TL>(wm, mb, ms, l0, st->sAw[0], st->sBw[0], &st->mbar[0]);
                 if (l0 + TL <= L) tma_weights<TL>(wm, mb, ms, l0 + TL, st->sAw[1], st->sBw[1], &st->mbar[1]);
@@ -141,7 +176,7 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
         }
 
         int tix = 0;
-        for (int ts = l0; ts <= L; ts += TL, ++tix) {
+        for (int ts = l0; cta_live && ts <= L; ts += TL, ++tix) {
             const int buf = tix & 1;
             bool ok = true;
             if (TMA) {
@@ -247,14 +282,14 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
                 sm.sT[i] = __double_as_longlong(WG_EPS_SUM / sg);
             }
             __syncthreads();
-            const int nl = min(TL, L + 1 - ts);
+            const int nl = warp_live ? min(TL, L + 1 - ts) : 0;
             for (int i = 0; i < nl; ++i) {
                 const double2 fg = sm.sA[i];
                 const long long thr = sm.sT[i];
                 bool any = false;
 #pragma unroll
                 for (int c = 0; c < CPT; ++c) {
-                    if (!summing[c] && plain[c] && abs_ge(u[c], thr)) {
+                    if (!summing[c] && plain[c] && (!LMIN || ts + i >= lfirst[c]) && abs_ge(u[c], thr)) {
                         summing[c] = true;
                         lsum[c] = ts + i;
                     }
@@ -333,7 +368,7 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
                     if (!mirror_ok) raise_status(T.status, WG_DEVERR_GRID);
                     outn[jm] = (ang[c].bad || !mirror_ok) ? make_double2(nan, nan) : make_double2(nr, ni);
                 }
-                n_elem += (unsigned long long)(L + 1 - l0);
+                if (cta_live && warp_live) n_elem += (unsigned long long)(L + 1 - l0);
                 n_sum += (unsigned long long)(L + 1 - min(lsum[c], L + 1));
             }
         }

@@ -42,6 +42,7 @@ struct ConvArgs {
     double *c_out;    // interleaved complex [mb][ms][j]
     unsigned long long *counters;
     int k_lo = 0, k_hi = -1;  // chain columns k = ms (mb_max + 1) + mb in [k_lo, k_hi); k_hi < 0: all
+    double offset = 0.0;      // the l_min cut's offset (kernels built with the cut only)
 };
 
 struct DTableBwdArgs {
@@ -67,6 +68,7 @@ struct ConvBwdArgs {
 int launch_dtable_fp64(const DTableArgs &a, const Tables &t, void *stream);
 int launch_dtable_fp32x(const DTableArgs &a, const Tables &t, void *stream);
 int launch_conv_fp64(const ConvArgs &a, const Tables &t, void *stream);
+int launch_conv_fp64_lmin(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff, bool full);
 int launch_conv_fp64_full(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff);
 int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream);
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream);

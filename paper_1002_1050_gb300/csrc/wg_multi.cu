@@ -40,7 +40,7 @@ template <int TL, int K>
 struct SmemMulti {
     double2 sA[TL];          // (F0', G')   (phase 1: (F0, G))
     double2 sWd[K][TL];      // w^{(k)}_l (phase 1), then times sigma_l
-    float4 sW[K][TL];        // w^{(k)}_l sigma_l as float-float
+    float4 sW[K][TL];        // w^{(k)}_l sigma_l as float-float: (re hi, im hi, re lo, im lo)
     long long sT[TL];        // bit pattern of 1e-30 / sigma_l
     double sF2[TL];          // F2_l
     double sSig[TL + 1];     // sigma_{ts + i}
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(NT) conv_multi_kernel(MultiArgs A, Tables T, i
         const int l0 = mb > ms ? mb : ms;
 
         double u[CPT], up[CPT], cre[K][CPT], cim[K][CPT];
-        ff are[K][CPT], aim[K][CPT];
+        float2 ahi[K][CPT], alo[K][CPT];  // float-float (re, im) sums
         int nsc[CPT], lsum[CPT];
         bool plain[CPT], summing[CPT];
 #pragma unroll
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(NT) conv_multi_kernel(MultiArgs A, Tables T, i
 #pragma unroll
             for (int q = 0; q < K; ++q) {
                 cre[q][c] = cim[q][c] = 0.0;
-                are[q][c] = aim[q][c] = ff{0.f, 0.f};
+                ahi[q][c] = alo[q][c] = make_float2(0.f, 0.f);
             }
             summing[c] = false;
             lsum[c] = L + 1;
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(NT) conv_multi_kernel(MultiArgs A, Tables T, i
                     w.y *= sg;
                     if (SUM_FF) {
                         float4 wf;
-                        dbl_to_ff(w.x, wf.x, wf.y);
-                        dbl_to_ff(w.y, wf.z, wf.w);
+                        dbl_to_ff(w.x, wf.x, wf.z);
+                        dbl_to_ff(w.y, wf.y, wf.w);
                         sm.sW[q][i] = wf;
                     } else {
                         sm.sWd[q][i] = w;
@@ -191,10 +191,9 @@ __global__ void __launch_bounds__(NT) conv_multi_kernel(MultiArgs A, Tables T, i
                         for (int q = 0; q < K; ++q) {
                             const float4 w = sm.sW[q][i];
 #pragma unroll
-                            for (int c = 0; c < CPT; ++c) {
-                                ff_mac(are[q][c], w.x, w.y, uu[c].hi, uu[c].lo);
-                                ff_mac(aim[q][c], w.z, w.w, uu[c].hi, uu[c].lo);
-                            }
+                            for (int c = 0; c < CPT; ++c)
+                                ff_mac2(ahi[q][c], alo[q][c], make_float2(w.x, w.y), make_float2(w.z, w.w),
+                                        uu[c].hi, uu[c].lo);
                         }
                     } else {
 #pragma unroll
@@ -230,8 +229,8 @@ __global__ void __launch_bounds__(NT) conv_multi_kernel(MultiArgs A, Tables T, i
                 for (int q = 0; q < K; ++q) {
                     double re = cre[q][c], im = cim[q][c];
                     if (SUM_FF) {
-                        re = (double)are[q][c].hi + (double)are[q][c].lo;
-                        im = (double)aim[q][c].hi + (double)aim[q][c].lo;
+                        re = (double)ahi[q][c].x + (double)alo[q][c].x;
+                        im = (double)ahi[q][c].y + (double)alo[q][c].y;
                     }
                     A.c[(COMBINE ? 0 : A.k0 + q) * A.sc + col * NB + jj[c]] =
                         ang[c].bad ? make_double2(nan, nan) : make_double2(re, im);

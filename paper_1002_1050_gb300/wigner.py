@@ -59,6 +59,7 @@ def load():
                 "wigner_conv_sum_host": [I, I, I, I, P, P, P, I, P, P],
                 "wigner_conv_sum_full": [I, I, I, I, P, P, P, I, P, P, P],
                 "wigner_conv_sum_multi": [I, I, I, I, I, P, P, P, I, I, I, P, P, P],
+                "wigner_conv_sum_lmin": [I, I, I, I, P, P, P, I, D, I, P, P, P],
                 "wigner_data_cube": [I, I, I, P, I, I, P, P],
                 "wigner_conv_sum_backward": [I, I, I, I, P, P, P, P, P, P, P, P, I, P],
                 "wigner_conv_sum_batched": [I, P, P],
@@ -210,6 +211,32 @@ def wigner_conv_sum_full(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, f
     with torch.cuda.device(beta.device):
         _check(lib.wigner_conv_sum_full(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
                                         _ptr(out), _ptr(counters), _stream(stream)))
+    return out
+
+
+def wigner_conv_sum_lmin(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, offset: float, form="fp64",
+                         full: bool = False, out: torch.Tensor | None = None,
+                         counters: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """wigner_conv_sum (full=False) or wigner_conv_sum_full (full=True) with the l_min cut of
+    Eq. lmin: each chain sums from l_min = (sqrt(m_sky^2 + m_b^2 - 2 m_sky m_b cos beta) -
+    offset) / sin beta; chains cut whole are not computed (their C is 0)."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    a = _dev_tensor(a, torch.complex128, "a")
+    b = _dev_tensor(b, torch.complex128, "b")
+    l_max, mb_max, ms_max, nb = _conv_shapes(beta, a, b)
+    shape = (mb_max + 1, 2 * ms_max + 1 if full else ms_max + 1, nb)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.complex128, device=beta.device)
+    _dev_tensor(out, torch.complex128, "out")
+    if tuple(out.shape) != shape:
+        raise ValueError("out has the wrong shape")
+    if counters is not None:
+        _dev_tensor(counters, torch.int64, "counters")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_conv_sum_lmin(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
+                                        float(offset), int(bool(full)), _ptr(out), _ptr(counters),
+                                        _stream(stream)))
     return out
 
 
@@ -489,4 +516,4 @@ def exported_symbols():
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
             "wigner_conv_sum_noalloc", "wigner_batch_plan_info", "wigner_plan_create", "wigner_plan_destroy",
             "wigner_last_error", "wigner_conv_sum_host", "wigner_conv_sum_full", "wigner_data_cube",
-            "wigner_conv_sum_multi"]
+            "wigner_conv_sum_multi", "wigner_conv_sum_lmin"]

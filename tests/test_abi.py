@@ -106,3 +106,13 @@ def test_multi_entry_point_validation(lib):
     assert lib.wigner_conv_sum_multi(8, 2, 8, 4, 2, FAKE, FAKE, FAKE, 1, 0, 5, FAKE, None, None) == -1
     assert lib.wigner_conv_sum_multi(8, 2, 8, 0, 2, None, None, None, 1, 0, 0, None, None, None) == 0
     assert lib.wigner_conv_sum_multi(8, 2, 8, 4, 0, FAKE, None, None, 1, 0, 0, FAKE, None, None) == 0
+
+
+def test_lmin_entry_point_validation(lib):
+    D = ctypes.c_double
+    # (l_max, mb, ms, nb, beta, a, b, form, offset, full, c, counters, stream)
+    assert lib.wigner_conv_sum_lmin(8, 9, 8, 4, FAKE, FAKE, FAKE, 0, D(10.0), 0, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_lmin(8, 2, 8, 4, FAKE, FAKE, FAKE, 0, D(float("nan")), 0, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_lmin(8, 2, 8, 4, FAKE, FAKE, FAKE, 1, D(10.0), 0, FAKE, None, None) == -6
+    assert lib.wigner_conv_sum_lmin(8, 2, 8, 4, None, FAKE, FAKE, 0, D(10.0), 1, FAKE, None, None) == -1
+    assert lib.wigner_conv_sum_lmin(8, 2, 8, 0, None, None, None, 0, D(10.0), 1, None, None, None) == 0
