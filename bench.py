@@ -737,7 +737,7 @@ def run_batched(args):
 
 # the dominant kernel as launched by wigner_conv_sum(form="fp64"); the committed DRAM
 # counters count only if they were taken on this same kernel
-FP64_KERNEL = "conv_fp64_kernel<256,2,128,false>, weights by TMA"
+FP64_KERNEL = "conv_fp64_kernel<256,2,128,false>, weights by TMA, 64 consecutive angles per warp"
 
 
 def _profile_traffic():

@@ -118,10 +118,10 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
     Angle ang[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        // LMIN: a warp's chains are 32 x CPT consecutive angles, so that the chains the cut
-        // removes (an interval of angles per column) tend to fill whole warps
-        jj[c] = LMIN ? chunk * NT * CPT + (tid >> 5) * (32 * CPT) + c * 32 + (tid & 31)
-                     : chunk * NT * CPT + c * NT + tid;
+        // a warp's chains are 32 x CPT consecutive angles: their 1e-30 crossings (and, with
+        // LMIN, their cuts) lie close together, so the warp starts its sum late when all
+        // its chains do and a cut tends to remove whole warps
+        jj[c] = chunk * NT * CPT + (tid >> 5) * (32 * CPT) + c * 32 + (tid & 31);
         valid[c] = jj[c] < NB;
         ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
         if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);

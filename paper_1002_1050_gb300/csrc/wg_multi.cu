@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT) conv_multi_kernel(MultiArgs A, Tables T, i
     Angle ang[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        jj[c] = chunk * NT * CPT + c * NT + tid;
+        jj[c] = chunk * NT * CPT + (tid >> 5) * (32 * CPT) + c * 32 + (tid & 31);  // a warp: 64 angles in a row
         valid[c] = jj[c] < NB;
         ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
         if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
