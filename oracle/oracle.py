@@ -72,6 +72,8 @@ def _open(path):
     lib.oracle_conv_sum_full_lmin.restype = I
     lib.oracle_conv_sum_full_sampled_lmin.argtypes = [I, I, I, I, P, P, P, I, P, D, P]
     lib.oracle_conv_sum_full_sampled_lmin.restype = I
+    lib.oracle_d_matrix.argtypes = [I, I, I, P, P]
+    lib.oracle_d_matrix.restype = I
     lib.oracle_l_first.argtypes = [I, I, I, D, D]
     lib.oracle_l_first.restype = I
     lib.oracle_conv_grad.argtypes = [I, I, I, I, P, P, P, P, P, P, P]
@@ -141,6 +143,17 @@ def d_column(l_max: int, mb: int, ms: int, beta) -> np.ndarray:
     out = np.empty((l_max + 1, beta.size), dtype=np.float64)
     if lib.oracle_d_column(l_max, mb, ms, beta.size, _ptr(beta), _ptr(out)) != 0:
         raise ValueError("oracle_d_column: invalid arguments")
+    return out
+
+
+def d_matrix(l: int, m_max: int, beta) -> np.ndarray:
+    """d[m][m' + l][j] = d^l_{m m'}(beta_j) for 0 <= m <= m_max, -l <= m' <= l: each element
+    the end of its own l-chain (the definition through the pinned chain code)."""
+    lib = _load()
+    beta = _f64(beta)
+    out = np.empty((m_max + 1, 2 * l + 1, beta.size), dtype=np.float64)
+    if lib.oracle_d_matrix(l, m_max, beta.size, _ptr(beta), _ptr(out)) != 0:
+        raise ValueError("oracle_d_matrix: invalid arguments")
     return out
 
 

@@ -295,6 +295,30 @@ double oracle_d_single(int l, int m, int mp, double beta) {
     return ctx.val;
 }
 
+/* The rows 0 <= m <= m_max of the matrix d^l(beta_j) at one l, every -l <= m' <= l:
+ * d_out[m][m' + l][j], shape (m_max+1, 2l+1, n_beta).  Each element is the end of its
+ * own l-chain from the general edge seed at l0 = max(|m|, |m'|) (the definition through
+ * the pinned chain code; no m-recursion, no ratios, no symmetry). */
+int oracle_d_matrix(int l, int m_max, int n_beta, const double *beta, double *d_out) {
+    if (l < 0 || l > 100000 || m_max < 0 || m_max > l || n_beta < 0) return -1;
+    angle_t *ang = (angle_t *)malloc(sizeof(angle_t) * (n_beta ? n_beta : 1));
+    for (int j = 0; j < n_beta; ++j) ang[j] = make_angle(beta[j]);
+    int nmp = 2 * l + 1;
+    long ncell = (long)(m_max + 1) * nmp;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long c = 0; c < ncell; ++c) {
+        int m = (int)(c / nmp), mp = (int)(c % nmp) - l;
+        for (int j = 0; j < n_beta; ++j) {
+            chain_spec cs = {l, m, mp, &ang[j], 1, 0};
+            one_ctx ctx = {l, 0.0};
+            run_chain(&cs, one_visit, &ctx);
+            d_out[(size_t)c * n_beta + j] = ctx.val;
+        }
+    }
+    free(ang);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* The l_min cut of Sec. 4.2.1 (Eq. lmin, its second, approximate line): in the */
 /* chain (m_b, m', beta) the terms with l below                                 */
