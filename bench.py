@@ -291,6 +291,9 @@ def run_ours(args):
     dtable = None
     if not args.skip_dtable:
         dtable = _dtable_block(W, dev, stream, args)
+    matrix = None
+    if not args.skip_matrix:
+        matrix = _matrix_block(W, dev, stream, args)
     lmin = None
     if not args.skip_lmin:
         lmin = _lmin_block(W, dev, stream, beta, a, b, out, mean_ms=total_ms / args.steps)
@@ -347,6 +350,7 @@ def run_ours(args):
         "fp32x": fp32x,
         "grad": grad,
         "dtable": dtable,
+        "matrix": matrix,
         "lmin": lmin,
         "multi": multi,
         "cube": cube,
@@ -572,6 +576,54 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
             "polarised_total_3": {"ms_per_launch": ms_pol, "vs_separate_calls": 3 * mean_ms / ms_pol}}
 
 
+def _matrix_block(W, dev, stream, args):
+    """The full-matrix evaluator (Sec. 3.1) at l = 1024, every row 0 <= m <= 1024 and every
+    -l <= m' <= l, at 256 Gauss-Legendre angles (4.30 GB of float64), and the spherical
+    harmonics up to l = 4096, m <= 64 at 2048 angles: time per launch, elements per second,
+    the write rate against the measured copy bandwidth and, for the matrix, the FP64 pipe
+    (two FMAs and two multiplies per element of Eq. mrec)."""
+    import torch
+    from paper_1002_1050_gb300 import inputs as I
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    l, nb = args.matrix_l, args.matrix_n_beta
+    beta = torch.from_numpy(I.beta_gauss_legendre(nb)[0]).to(dev)
+    out = torch.empty((nb, l + 1, 2 * l + 1), dtype=torch.float64, device=dev)
+    ms_m = timed(lambda: W.wigner_d_matrix(beta, l, out=out), 3)
+    W.check_device_status()
+    elems = out.numel()
+    peak_gbs, peak_src = _hbm_peak_gbs()
+    fp64_elem_peak = 152 * 2 * 2070e6 / 4.0  # FP64 lanes per second / DP instructions per element
+    del out
+    lt, mt, nt = 4096, 64, 2048
+    theta = torch.from_numpy(I.beta_gauss_legendre(nt)[0]).to(dev)
+    y = torch.empty((mt + 1, lt + 1, nt), dtype=torch.float64, device=dev)
+    ms_y = timed(lambda: W.wigner_ylm(theta, lt, mt, out=y), 3)
+    W.check_device_status()
+    ny = y.numel()
+    del y
+    torch.cuda.empty_cache()
+    return {"workload": f"d^l_{{m m'}} at l={l}, all 0<=m<={l}, -{l}<=m'<={l}, {nb} GL angles; "
+                        "Y_l^m for l<=4096, m<=64, 2048 GL angles",
+            "matrix": {"ms_per_launch": ms_m, "elements_per_s": elems / (ms_m / 1e3),
+                       "write_gb_per_s": elems * 8 / (ms_m / 1e3) / 1e9, "hbm_peak_gbs": peak_gbs,
+                       "hbm_frac": elems * 8 / (ms_m / 1e3) / 1e9 / peak_gbs,
+                       "fp64_frac": elems / (ms_m / 1e3) / fp64_elem_peak,
+                       "fp64_note": "4 DP instructions per element (Eq. mrec) against 152 SMs x 2 lanes x 2070 MHz"},
+            "ylm": {"ms_per_launch": ms_y, "elements_per_s": ny / (ms_y / 1e3),
+                    "write_gb_per_s": ny * 8 / (ms_y / 1e3) / 1e9, "hbm_peak_source": peak_src}}
+
+
 def _lmin_block(W, dev, stream, beta, a, b, out, mean_ms):
     """The l_min cut of Eq. lmin on the L=4096 workload at the paper's offsets (l_max/20,
     30, 15): time per launch, share of the nominal elements evaluated, and the residual
@@ -771,6 +823,9 @@ def main(argv=None):
     p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
     p.add_argument("--skip-grad", action="store_true", help="skip the forward/adjoint timing")
     p.add_argument("--skip-dtable", action="store_true", help="skip the d-table timing")
+    p.add_argument("--skip-matrix", action="store_true", help="skip the full-matrix and Y_lm timing")
+    p.add_argument("--matrix-l", type=int, default=1024, help="l of the full-matrix timing")
+    p.add_argument("--matrix-n-beta", type=int, default=256, help="angles of the full-matrix timing")
     p.add_argument("--skip-lmin", action="store_true", help="skip the l_min-cut timing")
     p.add_argument("--skip-multi", action="store_true", help="skip the several-column timing")
     p.add_argument("--skip-cube", action="store_true", help="skip the full-sum and data-cube timing")

@@ -183,6 +183,35 @@ int wigner_data_cube(int mb_max, int ms_max, int n_beta, const wg_c64 *c_full, i
                      double *cube, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * wigner_d_matrix -- rows of the whole matrix d^l(beta) at one l (the evaluator of
+ * Sec. 3.1): d_out[j][m][m' + l] = d^l_{m m'}(beta_j) for 0 <= m <= m_max, -l <= m' <= l;
+ * float64, shape (n_beta, m_max+1, 2l+1) (one matrix per angle), 8-byte aligned,
+ * overwritten.  The rows m < 0 follow from d_{-m,-m'} = (-1)^{m-m'} d_{m m'}.
+ *   Each row runs the three-term relation in m' (Eq. mrec) in its stable direction
+ *   (Sec. 2, Eq. classiccond): from m' = l down to m* = round(m cos beta), the centre of
+ *   the classical band, and from m' = -l up to m* - 1 (as the same run at pi - beta),
+ *   both from the exact edge seeds d^l_{m,+-l} of Eqs. ini1-ini2 in scaled doubles
+ *   (Sec. 3.2).  This replaces the paper's ratios anchored at m' = 0, which lose accuracy
+ *   below the band when m > 0 and sin beta is small.  beta = 0 gives the identity.
+ *   One warp runs 32 consecutive rows of one angle, so a single angle fills the GPU
+ *   once m_max is in the thousands.
+ *   counters: optional, [0] += (m_max+1)(2l+1) n_beta.
+ *   Errors: WG_ERR_ARG (l outside [0, WG_LMAX], m_max outside [0, l], pointers).
+ * ------------------------------------------------------------------------- */
+int wigner_d_matrix(int l, int m_max, int n_beta, const double *beta, double *d_out,
+                    wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * wigner_ylm -- the polar part of the spherical harmonics (Sec. 2: d^l_{m0} with the
+ * normalisation of Y_l^m): out[m][l][j] = sqrt((2l+1)/(4 pi)) d^l_{m 0}(theta_j), so that
+ * Y_l^m(theta, phi) = out[m][l][j] e^{i m phi} (Condon-Shortley phase); zero for l < m.
+ *   float64, shape (m_max+1, l_max+1, n_theta), overwritten; 0 <= m_max <= l_max.
+ *   Computed by the l-recursion of wigner_d_table (m_sky = 0) with the normalisation
+ *   applied as each value is stored.  Errors: as wigner_d_table.
+ * ------------------------------------------------------------------------- */
+int wigner_ylm(int l_max, int m_max, int n_theta, const double *theta, double *out, void *stream);
+
+/* ---------------------------------------------------------------------------
  * wigner_conv_sum_lmin -- the sum of Eq. convdef with the l_min cut of Sec. 4.2.1
  * (Eq. lmin, its approximate line): each chain (m_b, m_sky, beta_j) sums from
  *   l_min = (sqrt(m_sky^2 + m_b^2 - 2 m_sky m_b cos beta_j) - offset) / sin beta_j

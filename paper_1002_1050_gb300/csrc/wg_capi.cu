@@ -286,6 +286,21 @@ int wigner_d_table(int l_max, int mb_max, int ms_max, int n_beta, const double *
     }
 }
 
+int wigner_ylm(int l_max, int m_max, int n_theta, const double *theta, double *out, void *stream) {
+    try {
+        WG_TRY(check_orders(l_max, m_max, 0, n_theta));
+        if (n_theta == 0) return WG_OK;
+        WG_TRY(check_ptr(theta, 8, "theta"));
+        WG_TRY(check_ptr(out, 8, "out"));
+        wg::Tables t;
+        WG_TRY(get_tables(l_max, &t));
+        wg::DTableArgs a{l_max, m_max, 0, n_theta, theta, out, nullptr};
+        return launch_rc(wg::launch_ylm(a, t, stream), "ylm launch");
+    } catch (const std::bad_alloc &) {
+        return fail(WG_ERR_ALLOC, "host allocation failed");
+    }
+}
+
 int wigner_d_table_backward(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
                             const double *grad_d, double *grad_beta, void *stream) {
     try {

@@ -11,7 +11,10 @@
 
 namespace wg {
 
-template <int NT, int TL>
+// YLM: each d^l is stored times sqrt((2l+1)/(4 pi)): with ms_max = 0 the table is then the
+// theta part of the spherical harmonics, Y_l^m(theta, phi) = sqrt((2l+1)/(4 pi)) d^l_{m0}(theta)
+// e^{i m phi} (the Condon-Shortley phase comes with d).
+template <int NT, int TL, bool YLM = false>
 __global__ void __launch_bounds__(NT) dtable_fp64_kernel(DTableArgs A, Tables T) {
     const int col = blockIdx.x;
     const int mb = col / (A.ms_max + 1), ms = col % (A.ms_max + 1);
@@ -33,7 +36,7 @@ __global__ void __launch_bounds__(NT) dtable_fp64_kernel(DTableArgs A, Tables T)
     int n = t.bad ? 0 : s.n;
     bool plain = t.bad ? true : s.plain;
 
-    __shared__ double sF0[TL], sG[TL], sF2[TL];
+    __shared__ double sF0[TL], sG[TL], sF2[TL], sN[YLM ? TL : 1];
     for (int ts = l0; ts <= L; ts += TL) {
         __syncthreads();
         for (int i = threadIdx.x; i < TL; i += NT) {
@@ -43,12 +46,16 @@ __global__ void __launch_bounds__(NT) dtable_fp64_kernel(DTableArgs A, Tables T)
             sF0[i] = f0;
             sG[i] = g;
             sF2[i] = f2;
+            if (YLM) sN[i] = sqrt((double)(2 * l + 1) * WG_INV_4PI);
         }
         __syncthreads();
         const int nl = min(TL, L + 1 - ts);
         for (int i = 0; i < nl; ++i) {
             const int l = ts + i;
-            if (valid) out[(size_t)l * NB + j] = plain ? cur : scaled_to_double(cur, n);
+            if (valid) {
+                const double v = plain ? cur : scaled_to_double(cur, n);
+                out[(size_t)l * NB + j] = YLM ? v * sN[i] : v;
+            }
             if (l < L) {
                 const double y = fma(sF0[i], t.cb, -sG[i]);
                 const double nx = fma(y, cur, -(sF2[i] * prev));
@@ -70,6 +77,15 @@ int launch_dtable_fp64(const DTableArgs &a, const Tables &t, void *stream) {
     const int ncol = (a.mb_max + 1) * (a.ms_max + 1);
     dim3 grid(ncol, (a.n_beta + NT - 1) / NT);
     dtable_fp64_kernel<NT, TL><<<grid, NT, 0, (cudaStream_t)stream>>>(a, t);
+    return (int)cudaGetLastError();
+}
+
+// out[m][l][j] = sqrt((2l+1)/(4 pi)) d^l_{m0}(theta_j) (a.ms_max must be 0)
+int launch_ylm(const DTableArgs &a, const Tables &t, void *stream) {
+    constexpr int NT = 64, TL = 128;
+    if (a.n_beta == 0) return 0;
+    dim3 grid(a.mb_max + 1, (a.n_beta + NT - 1) / NT);
+    dtable_fp64_kernel<NT, TL, true><<<grid, NT, 0, (cudaStream_t)stream>>>(a, t);
     return (int)cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 // kept in [2^-90, 2^90] that is n >= -9
 #define WG_PLAIN_MIN_N (-9)
 #define WG_PI_HI 3.141592653589793115997963468544185161590576171875 /* the double nearest pi */
+#define WG_INV_4PI 0.07957747154594766788 /* 1 / (4 pi), the spherical-harmonic normalisation */
 // threshold of Sec. 4.2.1: terms are summed from the first l with |d| >= 1e-30
 #define WG_EPS_SUM 1e-30
 
@@ -68,6 +69,7 @@ struct ConvBwdArgs {
 int launch_dtable_fp64(const DTableArgs &a, const Tables &t, void *stream);
 int launch_dtable_fp32x(const DTableArgs &a, const Tables &t, void *stream);
 int launch_conv_fp64(const ConvArgs &a, const Tables &t, void *stream);
+int launch_ylm(const DTableArgs &a, const Tables &t, void *stream);
 int launch_conv_fp64_lmin(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff, bool full);
 int launch_conv_fp64_full(const ConvArgs &a, const Tables &t, void *stream, bool sum_ff);
 int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream);

@@ -60,6 +60,8 @@ def load():
                 "wigner_conv_sum_full": [I, I, I, I, P, P, P, I, P, P, P],
                 "wigner_conv_sum_multi": [I, I, I, I, I, P, P, P, I, I, I, P, P, P],
                 "wigner_conv_sum_lmin": [I, I, I, I, P, P, P, I, D, I, P, P, P],
+                "wigner_d_matrix": [I, I, I, P, P, P, P],
+                "wigner_ylm": [I, I, I, P, P, P],
                 "wigner_data_cube": [I, I, I, P, I, I, P, P],
                 "wigner_conv_sum_backward": [I, I, I, I, P, P, P, P, P, P, P, P, I, P],
                 "wigner_conv_sum_batched": [I, P, P],
@@ -211,6 +213,43 @@ def wigner_conv_sum_full(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, f
     with torch.cuda.device(beta.device):
         _check(lib.wigner_conv_sum_full(l_max, mb_max, ms_max, nb, _ptr(beta), _ptr(a), _ptr(b), _form(form),
                                         _ptr(out), _ptr(counters), _stream(stream)))
+    return out
+
+
+def wigner_d_matrix(beta: torch.Tensor, l: int, m_max: int | None = None, out: torch.Tensor | None = None,
+                    counters: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """d[j][m][m' + l] = d^l_{m m'}(beta_j) for 0 <= m <= m_max (default l), -l <= m' <= l."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    m_max = l if m_max is None else m_max
+    shape = (beta.numel(), m_max + 1, 2 * l + 1)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=beta.device)
+    _dev_tensor(out, torch.float64, "out")
+    if tuple(out.shape) != shape:
+        raise ValueError("out has the wrong shape")
+    if counters is not None:
+        _dev_tensor(counters, torch.int64, "counters")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_d_matrix(l, m_max, beta.numel(), _ptr(beta), _ptr(out), _ptr(counters),
+                                   _stream(stream)))
+    return out
+
+
+def wigner_ylm(theta: torch.Tensor, l_max: int, m_max: int | None = None, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """y[m][l][j] = sqrt((2l+1)/(4 pi)) d^l_{m0}(theta_j): Y_l^m(theta, phi) = y[m][l][j] e^{i m phi}."""
+    lib = load()
+    theta = _dev_tensor(theta, torch.float64, "theta")
+    m_max = l_max if m_max is None else m_max
+    shape = (m_max + 1, l_max + 1, theta.numel())
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=theta.device)
+    _dev_tensor(out, torch.float64, "out")
+    if tuple(out.shape) != shape:
+        raise ValueError("out has the wrong shape")
+    with torch.cuda.device(theta.device):
+        _check(lib.wigner_ylm(l_max, m_max, theta.numel(), _ptr(theta), _ptr(out), _stream(stream)))
     return out
 
 
@@ -516,4 +555,4 @@ def exported_symbols():
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
             "wigner_conv_sum_noalloc", "wigner_batch_plan_info", "wigner_plan_create", "wigner_plan_destroy",
             "wigner_last_error", "wigner_conv_sum_host", "wigner_conv_sum_full", "wigner_data_cube",
-            "wigner_conv_sum_multi", "wigner_conv_sum_lmin"]
+            "wigner_conv_sum_multi", "wigner_conv_sum_lmin", "wigner_d_matrix", "wigner_ylm"]

@@ -116,3 +116,14 @@ def test_lmin_entry_point_validation(lib):
     assert lib.wigner_conv_sum_lmin(8, 2, 8, 4, FAKE, FAKE, FAKE, 1, D(10.0), 0, FAKE, None, None) == -6
     assert lib.wigner_conv_sum_lmin(8, 2, 8, 4, None, FAKE, FAKE, 0, D(10.0), 1, FAKE, None, None) == -1
     assert lib.wigner_conv_sum_lmin(8, 2, 8, 0, None, None, None, 0, D(10.0), 1, None, None, None) == 0
+
+
+def test_matrix_and_ylm_validation(lib):
+    assert lib.wigner_d_matrix(-1, 0, 4, FAKE, FAKE, None, None) == -1
+    assert lib.wigner_d_matrix(5, 6, 4, FAKE, FAKE, None, None) == -1      # m_max > l
+    assert lib.wigner_d_matrix(5, 2, 4, None, FAKE, None, None) == -1
+    assert lib.wigner_d_matrix(5, 2, 4, FAKE, P(0x1004), None, None) == -1  # misaligned
+    assert lib.wigner_d_matrix(5, 2, 0, None, None, None, None) == 0
+    assert lib.wigner_ylm(5, 6, 4, FAKE, FAKE, None) == -1
+    assert lib.wigner_ylm(5, 2, 4, None, FAKE, None) == -1
+    assert lib.wigner_ylm(5, 2, 0, None, None, None) == 0
