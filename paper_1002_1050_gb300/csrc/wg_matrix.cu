@@ -16,7 +16,8 @@
 // 2^90) exactly as in the l-recursion.  One step (Eq. mrec solved for d_{m,k-1}):
 //   d_{k-1} = (2 (k cos x - m) / sin x) d_k / A_k - (C_k / A_k) d_{k+1},
 //   A_k = sqrt((l+k)(l-k+1)),  C_k = sqrt((l-k)(l+k+1)),
-// with k, 1/A_k and C_k/A_k per k in shared memory: two FMAs and two multiplies per element.
+// with k, 1/A_k and C_k/A_k per k in shared memory: two FMAs and two multiplies per element
+// (1/A_k from the P_i table of Sec. 4.2.2, C_k/A_k with one square root per k and CTA).
 //
 // Work split: a CTA takes one angle, one side and 32 x W consecutive rows m; lane i of a
 // warp runs row m0 + i.  All lanes start at k = l and their stops differ by at most
@@ -40,6 +41,7 @@ struct MatrixArgs {
     unsigned long long *counters;
 };
 
+
 constexpr int MX_TK = 32;  // orders per tile (= lanes, for the staged transpose)
 
 template <int W>
@@ -57,9 +59,14 @@ __global__ void __launch_bounds__(32 * W) dmatrix_kernel(MatrixArgs A, Tables T)
     __shared__ double sK[MX_TK], sInvA[MX_TK], sCA[MX_TK];
     __shared__ double sStage[W][32][MX_TK + 1];
     __shared__ int sStop[W][32];
+    __shared__ Angle sAng;
 
-    const Angle t = make_angle(A.beta[j]);
-    if (threadIdx.x == 0 && side == 0 && blockIdx.y == 0 && t.bad) raise_status(T.status, WG_DEVERR_BETA);
+    if (threadIdx.x == 0) {  // one angle per CTA: its trigonometry once
+        sAng = make_angle(A.beta[j]);
+        if (side == 0 && blockIdx.y == 0 && sAng.bad) raise_status(T.status, WG_DEVERR_BETA);
+    }
+    __syncthreads();
+    const Angle t = sAng;
     const int mstar = (int)rint((double)m * t.cb);  // centre of the classical band of row m
     Angle x = t;                                    // side 1: the mirrored angle pi - beta
     if (side) {
@@ -86,8 +93,8 @@ __global__ void __launch_bounds__(32 * W) dmatrix_kernel(MatrixArgs A, Tables T)
         if (threadIdx.x < MX_TK) {
             const int kk = ts - threadIdx.x;
             double ia = 0.0, ca = 0.0;
-            if (kk > -l && kk <= l) {
-                ia = 1.0 / sqrt((double)(l + kk) * (double)(l - kk + 1));
+            if (kk > -l && kk <= l) {  // 1/A_k = P_{l+k-1} P_{l-k}, P_i = 1/sqrt(i+1) (Sec. 4.2.2 table)
+                ia = T.P[l + kk - 1] * T.P[l - kk];
                 ca = sqrt((double)(l - kk) * (double)(l + kk + 1)) * ia;
             }
             sK[threadIdx.x] = (double)kk;
