@@ -44,6 +44,15 @@ struct MatrixArgs {
 
 constexpr int MX_TK = 32;  // orders per tile (= lanes, for the staged transpose)
 
+// The stored value of a chain in scaled mode, mant * 2^(90 n), by integer arithmetic on
+// the exponent field (no FP64 instruction, so the plain path costs nothing when the
+// compiler evaluates both sides): exact while the result is a normal double; a result
+// below 2^-1022 (the subnormal range) is stored as 0.
+__device__ __forceinline__ double scaled_store(double mant, int n) {
+    const int e = biased_exp(mant) + 90 * n;  // the result's biased exponent (n < 0; 0 stays below 1)
+    return e >= 1 ? exp_shift(mant, 90 * n) : 0.0;
+}
+
 template <int W>
 __global__ void __launch_bounds__(32 * W) dmatrix_kernel(MatrixArgs A, Tables T) {
     const int j = blockIdx.x;
@@ -112,7 +121,7 @@ __global__ void __launch_bounds__(32 * W) dmatrix_kernel(MatrixArgs A, Tables T)
             else if (pole)
                 v = (side == 0 && k == m) ? 1.0 : 0.0;
             else
-                v = plain ? cur : scaled_to_double(cur, n);
+                v = plain ? cur : scaled_store(cur, n);
             sStage[warp][lane][i] = v;
             if (k > stop && !pole) {  // Eq. mrec for d_{k-1}
                 const double b = fma(sK[i], cxs, -ms) * sInvA[i];
