@@ -319,6 +319,16 @@ __device__ __forceinline__ double scaled_to_double(double mant, int n) {
     return scalbn(mant, 90 * n);
 }
 
+// The value to store for a chain in scaled mode (n < 0), mant * 2^(90 n), by integer
+// arithmetic on the exponent field: no FP64 instruction, so a store that selects between
+// the plain and the scaled value costs nothing on the FP64 pipe when the compiler
+// evaluates both sides.  Exact while the result is a normal double; a result below
+// 2^-1022 (the subnormal range) is stored as 0.
+__device__ __forceinline__ double scaled_store(double mant, int n) {
+    const int e = biased_exp(mant) + 90 * n;  // the result's biased exponent (0 stays below 1)
+    return e >= 1 ? exp_shift(mant, 90 * n) : 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // Scaled-mode maintenance after a step (integer pipe only, except the one-time
 // conversion to plain doubles).  (cur, prev) share the exponent n.

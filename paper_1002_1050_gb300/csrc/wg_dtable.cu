@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(NT) dtable_fp64_kernel(DTableArgs A, Tables T)
         for (int i = 0; i < nl; ++i) {
             const int l = ts + i;
             if (valid) {
-                const double v = plain ? cur : scaled_to_double(cur, n);
+                const double v = plain ? cur : scaled_store(cur, n);
                 out[(size_t)l * NB + j] = YLM ? v * sN[i] : v;
             }
             if (l < L) {

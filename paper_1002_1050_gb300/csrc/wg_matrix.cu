@@ -44,14 +44,6 @@ struct MatrixArgs {
 
 constexpr int MX_TK = 32;  // orders per tile (= lanes, for the staged transpose)
 
-// The stored value of a chain in scaled mode, mant * 2^(90 n), by integer arithmetic on
-// the exponent field (no FP64 instruction, so the plain path costs nothing when the
-// compiler evaluates both sides): exact while the result is a normal double; a result
-// below 2^-1022 (the subnormal range) is stored as 0.
-__device__ __forceinline__ double scaled_store(double mant, int n) {
-    const int e = biased_exp(mant) + 90 * n;  // the result's biased exponent (n < 0; 0 stays below 1)
-    return e >= 1 ? exp_shift(mant, 90 * n) : 0.0;
-}
 
 template <int W>
 __global__ void __launch_bounds__(32 * W) dmatrix_kernel(MatrixArgs A, Tables T) {
