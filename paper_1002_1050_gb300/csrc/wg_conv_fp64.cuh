@@ -1,24 +1,25 @@
-// wg_conv_fp64.cu -- fused l-recursion + weighted l-sum in IEEE double
+// wg_conv_fp64.cuh -- fused l-recursion + weighted l-sum in IEEE double
 // (Sec. 4.1 Eq. convdef evaluated with the Sec. 3.2 recursion, Sec. 4.2.2 tables).
 //
 // Work decomposition
 //   A work item = (a group of G consecutive chain columns, a chunk of NT*CPT angles).
 //   Columns k are ordered m_sky-major (k = ms*(mb_max+1) + mb), so low k means a low
 //   start l0 = max(mb, ms) and a long chain; blockIdx.x walks the items in that
-//   order, longest first.  Each thread holds CPT chains (angles j = chunk*NT*CPT +
-//   c*NT + tid, c < CPT, so each warp's lanes hold consecutive angles) and keeps its
-//   per-angle quantities (cos beta, half-angle logs) in registers across the G columns.
-//   For each column the CTA walks l in tiles of TL: it builds the coefficient table
-//   (F0, F0*F1, F2) and the weights w_l = conj(b_{l,mb}) a_{l,ms} of the tile in
+//   order, longest first.  Each thread holds CPT chains; a warp holds 32*CPT
+//   consecutive angles (lane i: j0 + i and j0 + 32 + i for CPT = 2), and every thread
+//   keeps its per-angle quantities (cos beta, half-angle logs) in registers across
+//   the G columns.  For each column the CTA walks l in tiles of TL: it builds the
+//   coefficient table and the weights w_l = conj(b_{l,mb}) a_{l,ms} of the tile in
 //   shared memory once, and every chain of the CTA reads them as broadcasts.
 //
-// Per element (chain, l): y = fma(F0, cos b, -G), d' = fma(y, d, -(F2 d_prev))
-// (three FP64 instructions), then, from the first |d| >= 1e-30 on (Sec. 4.2.1),
-// C += w_l d (two FP64 FMAs).  The threshold test, the scaled-double bookkeeping
-// and the switch to plain doubles (Sec. 3.2) are integer operations on the
-// exponent field, so the FP64 pipe -- the scarce unit of this GPU -- only sees the
-// five arithmetic instructions.  A warp skips the sum only while none of its
-// chains has crossed the threshold.
+// Per element (chain, l): the chain is carried normalised, u^l = d^l / sigma_l, so
+// Eq. lrec takes two FP64 FMAs, y = fma(F0', cos b, -G'), u' = fma(y, u, -u_prev);
+// then, from the first |d| >= 1e-30 on (Sec. 4.2.1), C += (w_l sigma_l) u (two FP64
+// FMAs).  The threshold test, the scaled-double bookkeeping and the switch to plain
+// doubles (Sec. 3.2) are integer operations on the exponent field, so the FP64 pipe --
+// the scarce unit of this GPU -- sees only these FMAs.  A warp skips the sum only while
+// none of its chains has crossed the threshold; with consecutive angles in a warp the
+// crossings lie close together.
 #pragma once
 
 #include <cuda_runtime.h>
