@@ -20,6 +20,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -71,7 +72,10 @@ class ClockSampler:
     def __init__(self, uuid: str | None):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to WIGNER_CLOCKS_DIR (default: the system's temporary folder);
+        # the JSON line carries their summary
+        folder = os.environ.get("WIGNER_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
