@@ -17,7 +17,8 @@
  *
  * Conventions (all calls)
  *   - Orders: 0 <= m_b <= mb_max <= l_max, 0 <= m_sky <= ms_max <= l_max; l_max <= WG_LMAX.
- *     Only non-negative orders are computed.
+ *     Only non-negative orders are computed, except by wigner_conv_sum_full (every sky
+ *     order) and wigner_d_matrix (every m').
  *   - Angles: beta[j] in [0, pi], float64, device memory, n_beta >= 0 entries.
  *     beta = 0 and beta = pi are exact: d(0) = delta_{m m'}, d(pi) = (-1)^(l-m') delta_{m,-m'}.
  *     An angle outside [0, pi] (or NaN) makes the affected outputs NaN and records
