@@ -112,6 +112,9 @@ class Planted:
     def l_first(self, *args, **kw):
         return l_first(*args, _lib=self._lib, **kw)
 
+    def d_matrix(self, *args, **kw):
+        return d_matrix(*args, _lib=self._lib, **kw)
+
 
 def _ptr(x):
     return None if x is None else x.ctypes.data_as(ctypes.c_void_p)
@@ -146,10 +149,10 @@ def d_column(l_max: int, mb: int, ms: int, beta) -> np.ndarray:
     return out
 
 
-def d_matrix(l: int, m_max: int, beta) -> np.ndarray:
+def d_matrix(l: int, m_max: int, beta, _lib=None) -> np.ndarray:
     """d[m][m' + l][j] = d^l_{m m'}(beta_j) for 0 <= m <= m_max, -l <= m' <= l: each element
     the end of its own l-chain (the definition through the pinned chain code)."""
-    lib = _load()
+    lib = _lib or _load()
     beta = _f64(beta)
     out = np.empty((m_max + 1, 2 * l + 1, beta.size), dtype=np.float64)
     if lib.oracle_d_matrix(l, m_max, beta.size, _ptr(beta), _ptr(out)) != 0:

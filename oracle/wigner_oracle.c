@@ -309,7 +309,11 @@ int oracle_d_matrix(int l, int m_max, int n_beta, const double *beta, double *d_
     for (long c = 0; c < ncell; ++c) {
         int m = (int)(c / nmp), mp = (int)(c % nmp) - l;
         for (int j = 0; j < n_beta; ++j) {
+#if ORACLE_PLANT == 10
+            chain_spec cs = {l, mp, m, &ang[j], 1, 0}; /* planted: row and column orders swapped */
+#else
             chain_spec cs = {l, m, mp, &ang[j], 1, 0};
+#endif
             one_ctx ctx = {l, 0.0};
             run_chain(&cs, one_visit, &ctx);
             d_out[(size_t)c * n_beta + j] = ctx.val;
@@ -443,7 +447,11 @@ static void full_visit(void *vctx, int l, double mant, double dmant, int n) {
     const double *al = c->a + 2 * ((size_t)l * c->ms_max1 + am);
     double sre = al[0], sim = al[1];
     if (c->ms < 0) {  /* (-1)^m conj(a_{l,|m|}) */
+#if ORACLE_PLANT == 9
+        double sg = 1.0; /* planted: the (-1)^m of the real-sky relation dropped */
+#else
         double sg = (am & 1) ? -1.0 : 1.0;
+#endif
         sre = sg * al[0];
         sim = -sg * al[1];
     }

@@ -4,7 +4,8 @@ Each plant (ORACLE_PLANT=k in oracle/wigner_oracle.c, built into a separate
 library on the CPU) is a plausible slip: a dropped d^{l-1} term, a lost seed
 sign, cos for sin in the seed, a coefficient one order off, a pair not
 rescaled jointly, an unconjugated beam, a wrong beam column, the wrong sign of the
-cos term in the l_min cut (Eq. lmin).  The battery below
+cos term in the l_min cut (Eq. lmin), the (-1)^m of the real-sky relation dropped in
+the sum over every sky order, the orders of a full-matrix element swapped.  The battery below
 re-runs a compact version of the pins; the real oracle passes every check and
 every planted copy fails at least one.
 """
@@ -86,7 +87,34 @@ def _lmin_turning_point(orc):
     return True
 
 
-BATTERY = [_small_exact, _long_scaled_chain, _conv_beta_zero, _conv_gl_projection, _lmin_turning_point]
+def _full_sum_negative_orders(orc):
+    """The negative sky orders against the sum written out with exact d values."""
+    L, MB, MS = 6, 1, 4
+    beta = np.array([0.7, 2.1])
+    rng = np.random.default_rng(12)
+    a = rng.standard_normal((L + 1, MS + 1)) + 1j * rng.standard_normal((L + 1, MS + 1))
+    b = rng.standard_normal((L + 1, MB + 1)) + 1j * rng.standard_normal((L + 1, MB + 1))
+    full = orc.conv_sum_full(L, MB, MS, beta, a, b)
+    for mb in range(MB + 1):
+        for m in range(1, MS + 1):
+            for j, bt in enumerate(beta):
+                want = sum(np.conj(b[l, mb]) * (-1) ** m * np.conj(a[l, m]) * float(d_mp(l, mb, -m, bt, 30))
+                           for l in range(max(mb, m), L + 1))
+                if abs(full[mb, MS - m, j] - want) > 1e-12 * max(1.0, abs(want)):
+                    return False
+    return True
+
+
+def _matrix_l1(orc):
+    """The rows of d^1 in closed form (d^1_{10} = -sin b / sqrt 2)."""
+    b = 0.83
+    c, s = math.cos(b), math.sin(b)
+    want = np.array([[-s / math.sqrt(2), c, s / math.sqrt(2)], [(1 - c) / 2, -s / math.sqrt(2), (1 + c) / 2]])
+    return np.max(np.abs(orc.d_matrix(1, 1, np.array([b]))[:, :, 0] - want)) <= 1e-15
+
+
+BATTERY = [_small_exact, _long_scaled_chain, _conv_beta_zero, _conv_gl_projection, _lmin_turning_point,
+           _full_sum_negative_orders, _matrix_l1]
 
 
 def test_real_oracle_passes_battery():
@@ -94,7 +122,7 @@ def test_real_oracle_passes_battery():
         assert chk(O), chk.__name__
 
 
-@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("plant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_planted_mistake_is_caught(plant):
     orc = O.Planted(plant)
     assert not all(chk(orc) for chk in BATTERY), f"plant {plant} slipped through every pin"
