@@ -485,6 +485,9 @@ def _dtable_block(W, dev, stream, args):
         res[form] = {"us_per_launch": 1e3 * ms, "evals_per_s": elems / (ms / 1e3),
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": peak_src}}
+        if form == "fp64":  # the step's three FP64 instructions against the FP64 pipe
+            res[form]["fp64_pipe"] = {"dp_per_element": 3,
+                                      "frac": 3.0 * elems / (ms / 1e3) / (SMS * 2 * 2070e6)}
     del out, flush
     torch.cuda.empty_cache()
     return res
