@@ -37,6 +37,49 @@ L_MAX, MB_MAX, MS_MAX, N_BETA = 4096, 8, 4096, 2048
 SMS, FP64_FMA_PER_CLK_SM, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
+_PEAKS = {}
+
+
+def _measured_fma_peak(W, stream, pipe: int):
+    """FMA-pipe throughput measured on this GPU by the library's microbenchmark
+    (wigner_fma_peak): the best of a few launch shapes (independent chains per thread,
+    CTAs of 256 threads per SM), each launch ~0.1 s, timed with CUDA events.  pipe 0:
+    FP64, 1: FP32.  Returns (TFLOP/s, description) or (None, reason)."""
+    if pipe in _PEAKS:
+        return _PEAKS[pipe]
+    import torch
+
+    try:
+        best, best_cfg = 0.0, None
+        for ch, bps in ((8, 8), (16, 8), (4, 8), (8, 4)):
+            blocks = SMS * bps
+            iters = (40000 if pipe == 0 else 1600000) * 8 // ch
+            W.wigner_fma_peak(pipe, blocks, 256, 256, chains=ch)
+            torch.cuda.synchronize()
+            for _ in range(2):
+                p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                p0.record(stream)
+                _, ops = W.wigner_fma_peak(pipe, blocks, 256, iters, chains=ch)
+                p1.record(stream)
+                torch.cuda.synchronize()
+                tf = 2.0 * ops / (p0.elapsed_time(p1) / 1e3) / 1e12
+                if tf > best:
+                    best, best_cfg = tf, (ch, bps)
+        res = (best, f"measured: wigner_fma_peak {'FP64' if pipe == 0 else 'FP32'} FMA, best of 4 launch shapes "
+                     f"(best: {best_cfg[0]} chains/thread, {best_cfg[1]} CTAs of 256 threads per SM)")
+    except Exception as e:  # the microbenchmark is context, never fatal
+        res = (None, f"microbenchmark failed: {e}")
+    _PEAKS[pipe] = res
+    return res
+
+
+def _fp64_peak(W, stream):
+    """(peak TFLOP/s, source) of the FP64 FMA pipe: measured, else the derived figure."""
+    v, src = _measured_fma_peak(W, stream, 0)
+    if v:
+        return v, src
+    return FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (" + src + ")"
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -267,25 +310,16 @@ def run_ours(args):
         dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
     e2e_value = elems_rank * world * e2e_steps / (float(e2e_ms.item()) / 1e3)
 
-    # FMA-pipe microbenchmark (measured FP64 FMA throughput, for context)
-    peak_meas = None
-    try:
-        blocks, threads, iters = SMS * 8, 256, 4000
-        W.wigner_fma_peak(0, blocks, threads, 200)
-        torch.cuda.synchronize()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        _, ops = W.wigner_fma_peak(0, blocks, threads, iters)
-        p1.record(stream)
-        torch.cuda.synchronize()
-        peak_meas = 2.0 * ops / (p0.elapsed_time(p1) / 1e3) / 1e12
-    except Exception:
-        pass
+    # FMA-pipe microbenchmarks: the measured denominators of every FP64 / FP32 roofline
+    fp64_peak, fp64_src = _fp64_peak(W, stream)
+    fp32_meas, fp32_src = _measured_fma_peak(W, stream, 1)
 
     fp64s = None
     if not args.skip_fp64s:
         fp64s = _fp64s_block(W, beta, a, b, out, stream, args, elems_rank, mean_ms=total_ms / args.steps)
+    batched = None
+    if not args.skip_batched and world == 1:
+        batched = _batched_block(W, dev, stream, args)
     fp32x = None
     if not args.skip_fp32x:
         fp32x = _fp32x_block(W, dev, stream, args)
@@ -316,6 +350,12 @@ def run_ours(args):
     mean_launch_ms = float(np.mean(launch_ms))
     achieved = flops_launch / (mean_launch_ms / 1e3) / 1e12
     traffic = _profile_traffic()
+    rec = _profile_record()
+    executed = None
+    if rec.get("ncu_dfma_per_element"):
+        ex = 2.0 * rec["ncu_dfma_per_element"] * n_elem / (mean_launch_ms / 1e3) / 1e12
+        executed = {"dfma_per_element": rec["ncu_dfma_per_element"], "tflops": ex, "frac": ex / fp64_peak,
+                    "source": "DFMA per element from the committed ncu capture of this kernel"}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         e, dt, cores = _oracle_sample(beta_h, a_h, b_h, args.cpu_sample)
@@ -343,20 +383,22 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": achieved, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                      "kernel": FP64_KERNEL,
                      "flops_per_launch": flops_launch, "summed_elements": n_sum, "elements": n_elem,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
-                     "fma_microbench_tflops": peak_meas,
-                     "ncu_fp64_pipe_active": _profile_record().get("ncu_fp64_pipe_active"),
-                     "ncu_dfma_per_element": _profile_record().get("ncu_dfma_per_element"),
+                     "peak_source": fp64_src,
+                     "derived_peak": FP64_PEAK_TFLOPS,
+                     "executed": executed,
+                     "ncu_fp64_pipe_active": rec.get("ncu_fp64_pipe_active"),
                      "note": "achieved counts the paper's 5 flops per recursion element and 4 per summed "
-                             "element; the kernel executes 2 DFMA per step and the sum's 2 DFMA only on "
-                             "warp-steps past 1e-30, so achieved can exceed the pipe peak while the "
-                             "pipe itself is ncu_fp64_pipe_active busy"},
+                             "element (algorithmic); the kernel executes 2 DFMA per step and the sum's 2 DFMA "
+                             "only on warp-steps past 1e-30, so the algorithmic rate can exceed the pipe's; "
+                             "executed = the DFMAs the kernel actually issues, against the same measured peak"},
+        "fp32_fma_peak": {"tflops": fp32_meas, "source": fp32_src},
         "cpu_baseline": cpu,
         "fp64s": fp64s,
+        "batched": batched,
         "fp32x": fp32x,
         "grad": grad,
         "dtable": dtable,
@@ -396,13 +438,27 @@ def _fp64s_block(W, beta, a, b, out64, stream, args, elems, mean_ms):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.fp64s_steps
-    achieved = (5 * n_elem + 4 * n_sum) / (ms / 1e3) / 1e12
+    fp64_peak, fp64_src = _fp64_peak(W, stream)
+    fp32_peak, fp32_src = _measured_fma_peak(W, stream, 1)
+    fp32_peak = fp32_peak or FP32_PEAK_TFLOPS
+    rec_tf = 5 * n_elem / (ms / 1e3) / 1e12    # the recursion, on the FP64 pipe
+    ff_ops = FF_SUM_OPS * n_sum / (ms / 1e3)    # the float-float sum, FP32-pipe lane-operations per second
     return {"workload": WORKLOAD, "value": elems / (ms / 1e3), "unit": "evals/s", "ms_per_launch": ms,
             "dtype": "f64 recursion (2 FMA/step) + float-float sum on the FP32 pipe",
             "max_abs_diff_vs_fp64_kernel": diff, "speedup_vs_fp64_kernel": mean_ms / ms,
-            "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "note": "algorithmic flops over the FP64 peak; the sum runs on the FP32 pipe"}}
+            "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": rec_tf, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": rec_tf / fp64_peak, "peak_source": fp64_src,
+                         "note": "the recursion's 5 flops per element (the paper's count) over the FP64 pipe's "
+                                 "measured peak; the sum is on the FP32 pipe (fp32_pipe)"},
+            "fp32_pipe": {"lane_ops_per_summed_element": FF_SUM_OPS, "achieved_tops": ff_ops / 1e12,
+                          "peak_tops": fp32_peak / 2, "frac": ff_ops / 1e12 / (fp32_peak / 2),
+                          "peak_source": fp32_src + " (lane-operations: FLOP/s / 2)"}}
+
+
+# FP32-pipe lane-operations of one float-float product-accumulate pair (real and imaginary
+# parts of C += w u, two ff_mac of 15 operations each) plus the two multiplies of the split
+# of u into float-float (wg_common.cuh)
+FF_SUM_OPS = 32
 
 
 def _grad_block(W, dev, stream, args):
@@ -436,9 +492,15 @@ def _grad_block(W, dev, stream, args):
     ms_f = timed(lambda: W.wigner_conv_sum(beta, a, b, out=C), 2)
     ms_b = timed(lambda: W.wigner_conv_sum_backward(beta, a, b, C, G), 2)
     elems = I.n_elements(L, MB, MS, NB)
+    peak, src = _fp64_peak(W, stream)
+    ach = 5 * elems / (ms_b / 1e3) / 1e12
     return {"workload": "grad_l2048 (L=2048, m_b<=8, m_sky<=2048, 1024 uniform angles)",
             "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
-            "forward_evals_per_s": elems / (ms_f / 1e3), "backward_evals_per_s": elems / (ms_b / 1e3)}
+            "forward_evals_per_s": elems / (ms_f / 1e3), "backward_evals_per_s": elems / (ms_b / 1e3),
+            "roofline": {"bound": "alu", "pipe": "fp64_fma", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "peak_source": src,
+                         "note": "the recomputed recursion's 5 flops per element (the paper's count) over the "
+                                 "FP64 pipe; the adjoint's sums S and E run in float-float on the FP32 pipe"}}
 
 
 def _hbm_peak_gbs():
@@ -467,10 +529,16 @@ def _dtable_block(W, dev, stream, args):
     peak, peak_src = _hbm_peak_gbs()
     res = {"workload": "dtable_l256 (L=256, m_b<=4, m_sky<=256, 64 equispaced angles)", "elements": elems,
            "bytes_written": nbytes, "l2": "a 256 MB buffer is written between timed launches"}
+    ref64 = None
     for form in ("fp64", "fp32x"):
         W.wigner_d_table(beta, L, MB, MS, form=form, out=out)
         torch.cuda.synchronize()
         W.check_device_status()
+        if form == "fp64":
+            ref64 = out.clone()
+        else:
+            res["fp32x_max_abs_diff_vs_fp64_table"] = float((out - ref64).abs().max())
+            del ref64
         times = []
         for _ in range(args.dtable_steps):
             flush.fill_(1)
@@ -486,8 +554,10 @@ def _dtable_block(W, dev, stream, args):
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "peak_source": peak_src}}
         if form == "fp64":  # the step's three FP64 instructions against the FP64 pipe
+            peak64, src64 = _fp64_peak(W, stream)
             res[form]["fp64_pipe"] = {"dp_per_element": 3,
-                                      "frac": 3.0 * elems / (ms / 1e3) / (SMS * 2 * 2070e6)}
+                                      "frac": 3.0 * elems / (ms / 1e3) / (peak64 * 1e12 / 2),
+                                      "peak_source": src64}
     del out, flush
     torch.cuda.empty_cache()
     return res
@@ -616,7 +686,7 @@ def _matrix_block(W, dev, stream, args):
     W.check_device_status()
     elems = out.numel()
     peak_gbs, peak_src = _hbm_peak_gbs()
-    fp64_elem_peak = 152 * 2 * 2070e6 / 4.0  # FP64 lanes per second / DP instructions per element
+    fp64_elem_peak = _fp64_peak(W, stream)[0] * 1e12 / 2 / 4.0  # FP64 lanes per second / DP instructions per element
     del out
     lt, mt, nt = 4096, 64, 2048
     theta = torch.from_numpy(I.beta_gauss_legendre(nt)[0]).to(dev)
@@ -632,7 +702,7 @@ def _matrix_block(W, dev, stream, args):
                        "write_gb_per_s": elems * 8 / (ms_m / 1e3) / 1e9, "hbm_peak_gbs": peak_gbs,
                        "hbm_frac": elems * 8 / (ms_m / 1e3) / 1e9 / peak_gbs,
                        "fp64_frac": elems / (ms_m / 1e3) / fp64_elem_peak,
-                       "fp64_note": "4 DP instructions per element (Eq. mrec) against 152 SMs x 2 lanes x 2070 MHz"},
+                       "fp64_note": "4 DP instructions per element (Eq. mrec) against the measured FP64 FMA rate"},
             "ylm": {"ms_per_launch": ms_y, "elements_per_s": ny / (ms_y / 1e3),
                     "write_gb_per_s": ny * 8 / (ms_y / 1e3) / 1e9, "hbm_peak_source": peak_src}}
 
@@ -719,6 +789,9 @@ def _fp32x_block(W, dev, stream, args):
     W.check_device_status()
     flops = 5 * n_elem + 4 * n_sum
     achieved = flops / (ms_full / 1e3) / 1e12
+    peak32, src32 = _measured_fma_peak(W, stream, 1)
+    if not peak32:
+        peak32, src32 = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz (" + src32 + ")"
     del out, out64, out32
     torch.cuda.empty_cache()
     return {"workload": f"conv_fp32x_l8192 (L=8192, m_b<=16, m_sky<=8192, {beta.numel()} Gauss-Legendre angles)",
@@ -726,36 +799,33 @@ def _fp32x_block(W, dev, stream, args):
             "dtype": "f32 recursion + int32 exponent carry, float-float seeds and coefficients, compensated f32 sums",
             "rel_l2_vs_fp64_kernel": rel, "error_subset": "every 16th angle (512 of 8192)",
             "speedup_vs_fp64_kernel": ms64 / ms32, "speedup_subset_ms": {"fp64": ms64, "fp32x": ms32},
-            "roofline": {"bound": "alu", "pipe": "fp32_fma", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"}}
+            "roofline": {"bound": "alu", "pipe": "fp32_fma", "achieved": achieved, "peak": peak32,
+                         "unit": "TFLOP/s", "frac": achieved / peak32, "peak_source": src32,
+                         "derived_peak": FP32_PEAK_TFLOPS}}
 
 
-def run_batched(args):
-    """The batched workload: 64 uneven instances (l_max ~ U[128, 8192], m_b in {0,2,4,8,16},
-    n_beta ~ U[32, 4096] GL angles, FP64 or FP32 form with p = 1/2), one persistent
-    autotuned launch replayed from a CUDA graph, against one wigner_conv_sum launch per instance."""
+def _batched_block(W, dev, stream, args):
+    """The 64-instance uneven batch (l_max ~ U[128, 8192], m_b in {0,2,4,8,16}, n_beta ~
+    U[32, 4096] GL angles, FP64 or FP32 form with p = 1/2): one persistent autotuned launch
+    replayed from a CUDA graph against one wigner_conv_sum launch per instance, one timed
+    pass of each (a pass is ~50 s)."""
     import torch
-
-    _, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    import __graft_entry__ as g
-
-    g.build()
     from paper_1002_1050_gb300 import inputs as I
-    from paper_1002_1050_gb300 import wigner as W
 
     specs = I.batch_instances(n=args.batch_n, seed=0)
     a_full = torch.from_numpy(specs[0]["a_full"]).to(dev)
-    probs, elems = [], 0
+    probs, elems, e64, e32 = [], 0, 0, 0
     for sp in specs:
         L, MB = sp["l_max"], sp["mb_max"]
         probs.append((torch.from_numpy(sp["beta"]).to(dev), a_full[:L + 1, :L + 1].contiguous(),
                       torch.from_numpy(I.beam_blm(L, MB)).to(dev), sp["form"], None))
-        elems += I.n_elements(L, MB, L, sp["n_beta"])
+        n = I.n_elements(L, MB, L, sp["n_beta"])
+        elems += n
+        if sp["form"] == 0:
+            e64 += n
+        else:
+            e32 += n
     del a_full
-    stream = torch.cuda.current_stream(dev)
     outs = [torch.empty((p[2].shape[1], p[1].shape[1], p[0].numel()), dtype=torch.complex128, device=dev)
             for p in probs]
 
@@ -776,26 +846,49 @@ def run_batched(args):
     t0 = time.perf_counter()
     plan = W.BatchPlan([(p[0], p[1], p[2], p[3], o) for p, o in zip(probs, outs)], autotune=True)
     tune_s = time.perf_counter() - t0  # the autotuner also loads every kernel module
-    ms_sep = timed(per_instance, args.steps)
+    ms_sep = timed(per_instance, args.batch_steps)
     plan.run(use_graph=True)  # captures the graph
-    ms_graph = timed(lambda: plan.run(use_graph=True), args.steps)
+    ms_graph = timed(lambda: plan.run(use_graph=True), args.batch_steps)
     info = plan.info()
     W.check_device_status()
     plan.close()
+    n64 = sum(1 for sp in specs if sp["form"] == 0)
+    del outs, probs, plan
+    torch.cuda.empty_cache()
+    return {"workload": f"batched_uneven_{len(specs)} ({n64} FP64 + {len(specs) - n64} FP32-form instances, "
+                        "l_max~U[128,8192], m_b in {0,2,4,8,16}, n_beta~U[32,4096] GL angles)",
+            "elements": elems, "fp64_elements": e64, "fp32x_elements": e32,
+            "persistent_graph": {"ms_per_batch": ms_graph, "evals_per_s": elems / (ms_graph / 1e3), **info,
+                                 "autotune_s": tune_s},
+            "per_instance_launches": {"ms_per_batch": ms_sep, "evals_per_s": elems / (ms_sep / 1e3),
+                                      "launches": len(specs)},
+            "speedup_vs_per_instance": ms_sep / ms_graph, "timed_passes": args.batch_steps}
+
+
+def run_batched(args):
+    """The batched workload as the headline: the `batched` block of the default run, timed
+    over args.steps passes of each arm."""
+    import torch
+
+    _, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1002_1050_gb300 import wigner as W
+
+    args.batch_steps = args.steps
+    blk = _batched_block(W, dev, torch.cuda.current_stream(dev), args)
     if rank != 0:
         return 0
-    n64 = sum(1 for sp in specs if sp["form"] == 0)
-    line = {"metric": METRIC, "value": elems / (ms_graph / 1e3), "unit": "evals/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": 1, "ms_per_step": ms_graph, "higher_is_better": True,
+    pg = blk["persistent_graph"]
+    line = {"metric": METRIC, "value": pg["evals_per_s"], "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 1, "ms_per_step": pg["ms_per_batch"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed forms)", "data": "synthetic",
-            "config": {"workload": f"batched_uneven_{len(specs)} ({n64} FP64 + {len(specs) - n64} FP32-form "
-                                   "instances, l_max~U[128,8192], m_b in {0,2,4,8,16}, n_beta~U[32,4096])",
-                       "elements_per_step": elems},
-            "per_instance_launches": {"ms_per_batch": ms_sep, "value": elems / (ms_sep / 1e3),
-                                      "launches": len(specs)},
-            "persistent_graph": {"ms_per_batch": ms_graph, **info,
-                                 "autotune_s": tune_s},
-            "speedup_vs_per_instance": ms_sep / ms_graph}
+            "config": {"workload": blk["workload"], "elements_per_step": blk["elements"]},
+            "per_instance_launches": blk["per_instance_launches"], "persistent_graph": pg,
+            "speedup_vs_per_instance": blk["speedup_vs_per_instance"], "gpu_launches": args.steps}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -833,11 +926,13 @@ def main(argv=None):
     p.add_argument("--workload", choices=["conv_fp64_l4096", "batched"], default="conv_fp64_l4096",
                    help="batched: the 64-instance uneven batch (persistent launch vs per-instance)")
     p.add_argument("--batch-n", type=int, default=64)
+    p.add_argument("--batch-steps", type=int, default=1, help="timed passes of each arm in the batched block")
     p.add_argument("--cpu-sample", type=int, default=48, help="angles in the oracle's CPU-baseline sample")
     p.add_argument("--ref-sample", type=int, default=8, help="angles per step in the reference arm")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--skip-fp32x", action="store_true", help="skip the FP32-form measurement")
     p.add_argument("--skip-fp64s", action="store_true", help="skip the split-pipe FP64 measurement")
+    p.add_argument("--skip-batched", action="store_true", help="skip the 64-instance batch (about two minutes)")
     p.add_argument("--skip-grad", action="store_true", help="skip the forward/adjoint timing")
     p.add_argument("--skip-dtable", action="store_true", help="skip the d-table timing")
     p.add_argument("--skip-matrix", action="store_true", help="skip the full-matrix and Y_lm timing")

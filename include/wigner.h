@@ -336,12 +336,25 @@ int wigner_conv_sum_batched(int n, const wg_instance *inst, void *stream);
  *   capture, and do not overlap it with another call of this entry point on the same
  *   device: until it returns, the array is being written.  Later calls only read the
  *   array (its contents never change after set-up), so they may overlap one another.
- *   It keeps no status word: an angle outside [0, pi] shows only as NaN outputs.
+ *   The set-up also clears this entry point's own status word (a file-scope device
+ *   variable, like the tables) and waits for the device before the first launch, so the
+ *   first call may be made on any stream, blocking or not.
+ *   Device-side conditions go to that status word, which wigner_noalloc_status reads
+ *   and clears (never wigner_device_status, whose word is allocated): an angle outside
+ *   [0, pi] (its outputs NaN; WG_ERR_ARG) and a bounded TMA wait that gave up (the
+ *   abandoned outputs NaN; WG_ERR_TIMEOUT).  The word is shared by every call on the
+ *   device and keeps its bits until read.
  *   Calls no cudaMalloc, cudaFree or other allocating routine, on the host heap either.
  * ------------------------------------------------------------------------- */
 #define WG_NOALLOC_LMAX 8192
 int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
                             const wg_c64 *a, const wg_c64 *b, wg_c64 *c_out, void *stream);
+
+/* wigner_noalloc_status -- synchronises `stream`, then returns and clears the status word
+ * of wigner_conv_sum_noalloc on the current device: WG_OK, WG_ERR_TIMEOUT (a bounded wait
+ * gave up) or WG_ERR_ARG (an angle outside [0, pi]); WG_OK if the entry point has not run
+ * on this device.  Allocates nothing (symbol copies of one int). */
+int wigner_noalloc_status(void *stream);
 
 /* ---------------------------------------------------------------------------
  * Plans: reserve the library's device state up front.
@@ -383,13 +396,33 @@ int wigner_built_arch(void);
 
 /* ---------------------------------------------------------------------------
  * FMA-pipe microbenchmark (measures the roofline denominators of the path).
- *   pipe = 0: FP64 FMA, 1: FP32 FMA.  Runs `iters` iterations of `chains`
- *   independent FMA chains per thread on blocks x threads; writes a sink value per
- *   thread to sink (device, blocks*threads doubles) so the work cannot be elided.
- *   Returns the number of FMA lane-operations performed in *fma_ops (host).
+ *   pipe = 0: FP64 FMA, 1: FP32 FMA.  Runs `iters` iterations of `chains` (1, 2, 4, 8
+ *   or 16) independent FMA chains per thread on blocks x threads (threads <= 256, a
+ *   multiple of 32); writes a sink value per thread to sink (device, blocks*threads
+ *   doubles) so the work cannot be elided.  Returns the number of FMA lane-operations
+ *   performed in *fma_ops (host).
  * ------------------------------------------------------------------------- */
-int wigner_fma_peak(int pipe, int blocks, int threads, int iters, double *sink,
+int wigner_fma_peak(int pipe, int chains, int blocks, int threads, int iters, double *sink,
                     unsigned long long *fma_ops, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Test hooks for the failure paths (host side only; nothing here makes a GPU fault).
+ * wigner_debug_inject_alloc_failures: the library's next n device allocations (tables,
+ *   status word, adjoint workspace, batch plans, host-call buffers) fail as if the
+ *   device were out of memory, without calling the allocator: the call that needed the
+ *   memory returns WG_ERR_ALLOC and allocates nothing; n = 0 clears.  Process-wide.
+ * wigner_debug_set_wait_tries: the number of tries of each bounded mbarrier wait (the
+ *   TMA weight pipeline of the FP64 fused sums) in launches made from now on; default
+ *   2^20, 0 makes every such wait give up at once.  A wait that gives up records
+ *   WG_ERR_TIMEOUT in the status word (wigner_device_status, or wigner_noalloc_status
+ *   for wigner_conv_sum_noalloc), waits with the default limit for the copies it has
+ *   already issued, and writes NaN to the outputs its CTA abandons.  Process-wide.
+ * wigner_debug_wait_tries: the current value.
+ * Errors: WG_ERR_ARG for a negative argument.
+ * ------------------------------------------------------------------------- */
+int wigner_debug_inject_alloc_failures(int n);
+int wigner_debug_set_wait_tries(int tries);
+int wigner_debug_wait_tries(void);
 
 #ifdef __cplusplus
 }

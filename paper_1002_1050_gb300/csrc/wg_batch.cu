@@ -157,13 +157,16 @@ int upload_items(wg_batch_plan *p, const std::vector<Item> &items) {
     std::vector<int4> h(items.size());
     for (size_t i = 0; i < items.size(); ++i)
         h[i] = make_int4(items[i].inst, items[i].chunk, items[i].k_begin, items[i].k_end);
-    cudaError_t e = cudaMalloc(&p->d_items, h.size() * sizeof(int4));
+    cudaError_t e = wg::alloc_injected() ? cudaErrorMemoryAllocation : cudaMalloc(&p->d_items, h.size() * sizeof(int4));
     if (e != cudaSuccess) {
         p->d_items = nullptr;
         wg::set_last_error(std::string("cudaMalloc(batch items): ") + cudaGetErrorString(e), WG_ERR_ALLOC);
         return WG_ERR_ALLOC;
     }
     e = cudaMemcpy(p->d_items, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    // from pageable memory the copy may return before it has landed, and the plan runs
+    // on the caller's stream, which need not be ordered after the legacy stream
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         wg::set_last_error(std::string("cudaMemcpy(batch items): ") + cudaGetErrorString(e), WG_ERR_CUDA);
         return WG_ERR_CUDA;
@@ -363,7 +366,7 @@ int wigner_batch_plan_create(wg_batch_plan **plan, int n, const wg_instance *ins
                                  (const double *)I.b, (double *)I.c_out, nullptr};
         h[i].form = (int)I.form;
     }
-    cudaError_t e = cudaMalloc(&p->d_counter, sizeof(int));
+    cudaError_t e = wg::alloc_injected() ? cudaErrorMemoryAllocation : cudaMalloc(&p->d_counter, sizeof(int));
     if (e == cudaSuccess && n > 0) e = cudaMalloc(&p->d_insts, n * sizeof(wg::BatchInst));
     if (e != cudaSuccess) {
         wg::set_last_error(std::string("cudaMalloc(batch plan): ") + cudaGetErrorString(e), WG_ERR_ALLOC);
@@ -372,6 +375,7 @@ int wigner_batch_plan_create(wg_batch_plan **plan, int n, const wg_instance *ins
     }
     if (n > 0) {
         e = cudaMemcpy(p->d_insts, h.data(), n * sizeof(wg::BatchInst), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();  // see upload_items
         if (e != cudaSuccess) {
             wg::set_last_error(std::string("cudaMemcpy(batch plan): ") + cudaGetErrorString(e), WG_ERR_CUDA);
             free_plan(p);

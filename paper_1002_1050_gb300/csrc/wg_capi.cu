@@ -3,6 +3,7 @@
 // status word and error reporting.  Kernels live in the other translation units.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +49,10 @@ struct DevState {
 
 std::mutex g_mu;
 std::map<int, DevState> g_dev;
+
+// test hooks (wigner_debug_inject_alloc_failures, wigner_debug_set_wait_tries)
+std::atomic<int> g_inject_alloc{0};
+std::atomic<int> g_wait_tries{WG_WAIT_TRIES_DEFAULT};
 
 // Host-side construction of the constant tables (Sec. 4.2.2 and Sec. 3.2):
 //   ln n! for n <= 2 lcap + 1 as a double-double from long double lgamma,
@@ -113,6 +118,7 @@ int get_tables(int l_max, wg::Tables *t, DevState **out_state = nullptr) {
     if (s.status == nullptr) {
         int rc = check_device(dev);
         if (rc != WG_OK) return rc;
+        if (wg::alloc_injected()) return fail(WG_ERR_ALLOC, "cudaMalloc(status): injected allocation failure");
         e = cudaMalloc(&s.status, sizeof(int));
         if (e != cudaSuccess) {
             s.status = nullptr;
@@ -120,6 +126,9 @@ int get_tables(int l_max, wg::Tables *t, DevState **out_state = nullptr) {
         }
         e = cudaMemset(s.status, 0, sizeof(int));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        // the memset runs on the legacy stream: finish it before any stream may read the word
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize(status)");
     }
     if (s.lcap < l_max) {
         int lcap = 1024;
@@ -128,9 +137,13 @@ int get_tables(int l_max, wg::Tables *t, DevState **out_state = nullptr) {
         std::vector<double> h;
         build_tables(lcap, h);
         double *d = nullptr;
+        if (wg::alloc_injected()) return fail(WG_ERR_ALLOC, "cudaMalloc(tables): injected allocation failure");
         e = cudaMalloc(&d, h.size() * sizeof(double));
         if (e != cudaSuccess) return fail(WG_ERR_ALLOC, std::string("cudaMalloc(tables): ") + cudaGetErrorString(e));
         e = cudaMemcpy(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+        // a copy from pageable memory may return before its transfer has landed, and a
+        // kernel on a non-blocking stream is not ordered after it: wait for the device
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             cudaFree(d);
             return cuda_fail(e, "cudaMemcpy(tables)");
@@ -174,6 +187,7 @@ int get_workspace(size_t bytes, void **ws) {
         s.ws = nullptr;
         s.ws_bytes = 0;
         size_t want = bytes + bytes / 4;
+        if (wg::alloc_injected()) return fail(WG_ERR_ALLOC, "cudaMalloc(workspace): injected allocation failure");
         e = cudaMalloc(&s.ws, want);
         if (e != cudaSuccess) {
             s.ws = nullptr;
@@ -221,6 +235,13 @@ void set_last_error(const std::string &msg, int code) {
     g_code = code;
 }
 int tables_for(int l_max, Tables *t) { return get_tables(l_max, t); }
+bool alloc_injected() {
+    int n = g_inject_alloc.load();
+    while (n > 0)
+        if (g_inject_alloc.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+int wait_tries() { return g_wait_tries.load(); }
 }  // namespace wg
 
 extern "C" {
@@ -336,6 +357,7 @@ int wigner_conv_sum(int l_max, int mb_max, int ms_max, int n_beta, const double 
         WG_TRY(get_tables(l_max, &t));
         wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b,
                         (double *)c_out, counters};
+        ca.wait_tries = wg::wait_tries();
         if (form == WG_FP64) return launch_rc(wg::launch_conv_fp64(ca, t, stream), "conv_fp64 launch");
         if (form == WG_FP64S) return launch_rc(wg::launch_conv_fp64s(ca, t, stream), "conv_fp64s launch");
         return launch_rc(wg::launch_conv_fp32x(ca, t, stream), "conv_fp32x launch");
@@ -360,6 +382,7 @@ int wigner_conv_sum_full(int l_max, int mb_max, int ms_max, int n_beta, const do
         WG_TRY(get_tables(l_max, &t));
         wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b,
                         (double *)c_out, counters};
+        ca.wait_tries = wg::wait_tries();
         return launch_rc(wg::launch_conv_fp64_full(ca, t, stream, form == WG_FP64S), "conv_fp64_full launch");
     } catch (const std::bad_alloc &) {
         return fail(WG_ERR_ALLOC, "host allocation failed");
@@ -385,6 +408,7 @@ int wigner_conv_sum_lmin(int l_max, int mb_max, int ms_max, int n_beta, const do
         wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b,
                         (double *)c_out, counters};
         ca.offset = offset;
+        ca.wait_tries = wg::wait_tries();
         return launch_rc(wg::launch_conv_fp64_lmin(ca, t, stream, form == WG_FP64S, full != 0),
                          "conv_fp64_lmin launch");
     } catch (const std::bad_alloc &) {
@@ -460,14 +484,30 @@ int wigner_plan_create(wg_plan **plan, const wg_params *prm) {
 
 void wigner_plan_destroy(wg_plan *plan) { delete plan; }
 
-int wigner_fma_peak(int pipe, int blocks, int threads, int iters, double *sink, unsigned long long *fma_ops,
-                    void *stream) {
+int wigner_debug_inject_alloc_failures(int n) {
+    if (n < 0) return fail(WG_ERR_ARG, "n must be >= 0");
+    g_inject_alloc.store(n);
+    return WG_OK;
+}
+
+int wigner_debug_set_wait_tries(int tries) {
+    if (tries < 0) return fail(WG_ERR_ARG, "tries must be >= 0");
+    g_wait_tries.store(tries == 0 ? 0 : tries);
+    return WG_OK;
+}
+
+int wigner_debug_wait_tries(void) { return g_wait_tries.load(); }
+
+int wigner_fma_peak(int pipe, int chains, int blocks, int threads, int iters, double *sink,
+                    unsigned long long *fma_ops, void *stream) {
     if (pipe != 0 && pipe != 1) return fail(WG_ERR_ARG, "pipe must be 0 (FP64) or 1 (FP32)");
+    if (chains != 1 && chains != 2 && chains != 4 && chains != 8 && chains != 16)
+        return fail(WG_ERR_ARG, "chains must be 1, 2, 4, 8 or 16");
     if (blocks <= 0 || threads <= 0 || threads > 256 || (threads % 32) || iters <= 0)
         return fail(WG_ERR_ARG, "bad launch shape");
     WG_TRY(check_ptr(sink, 8, "sink"));
-    if (fma_ops) *fma_ops = (unsigned long long)blocks * threads * (unsigned long long)iters * 8ull;
-    return launch_rc(wg::launch_fma_peak(pipe, blocks, threads, iters, sink, stream), "fma_peak launch");
+    if (fma_ops) *fma_ops = (unsigned long long)blocks * threads * (unsigned long long)iters * (unsigned long long)chains;
+    return launch_rc(wg::launch_fma_peak(pipe, chains, blocks, threads, iters, sink, stream), "fma_peak launch");
 }
 
 }  // extern "C"

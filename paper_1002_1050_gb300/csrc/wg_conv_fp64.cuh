@@ -92,9 +92,31 @@ __device__ __forceinline__ int lmin_first(int L, int l0, int mb, int ms, const A
     return (int)ceil(x);
 }
 
+// The outputs of column k (and, FULL, of its mirrored order) for this thread's chains
+// set to NaN: the column was abandoned after a bounded wait gave up.
+template <int CPT, bool FULL>
+__device__ __forceinline__ void abandon_column(const ConvArgs &A, int k, const int *jj, const bool *valid) {
+    const int MB1 = A.mb_max + 1;
+    const int ms = k / MB1, mb = k - ms * MB1;
+    const int NB = A.n_beta;
+    const size_t NS = FULL ? (size_t)2 * A.ms_max + 1 : (size_t)A.ms_max + 1;
+    const size_t col = (size_t)mb * NS + (FULL ? (size_t)(A.ms_max + ms) : (size_t)ms);
+    double2 *out = reinterpret_cast<double2 *>(A.c_out) + col * NB;
+    double2 *outn = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * NS + (size_t)(A.ms_max - ms)) * NB;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+        if (!valid[c]) continue;
+        out[jj[c]] = make_double2(nan, nan);
+        if (FULL && ms > 0) outn[NB - 1 - jj[c]] = make_double2(nan, nan);
+    }
+}
+
 // TMA: the weights arrive by TMA (wm, st; the mbarriers initialised by the caller, their
-// phases in ph), else by plain loads.  Returns false if a TMA wait gave up (the status
-// word then has WG_DEVERR_TIMEOUT and no copy is left in flight).
+// phases in ph), else by plain loads.  Returns false if a TMA wait gave up after
+// A.wait_tries tries: the status word then has WG_DEVERR_TIMEOUT, the copies already
+// issued have been waited for (default limit), and the outputs of the abandoned
+// columns of this CTA's chains are NaN.
 // FULL: the sum over every sky order (the data cube of Sec. 4.1, m_sky from -ms_max to
 // ms_max) for a mirror-symmetric angle grid (beta_{N-1-j} = pi - beta_j).  The chain of
 // (m_b, m_sky) at beta_j also gives the order -m_sky at pi - beta_j through the
@@ -181,21 +203,24 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
             const int buf = tix & 1;
             bool ok = true;
             if (TMA) {
-                ok = mbar_wait(&st->mbar[buf], ph[buf]);
+                ok = mbar_wait(&st->mbar[buf], ph[buf], A.wait_tries);
                 if (ok) {
                     inflight[buf] = false;
                     ph[buf] ^= 1u;
                 }
             }
             if (!__syncthreads_and(ok)) {
-                // a TMA wait gave up: record it, give the copies in flight a bounded
-                // chance to land, and leave
+                // a TMA wait gave up: record it, let the copies already issued land (each
+                // drain wait with the default limit, whatever the launch's limit), mark
+                // this column and the group's later columns NaN for this CTA's chains,
+                // and leave
                 if (tid == 0) {
                     raise_status(T.status, WG_DEVERR_TIMEOUT);
                     for (int b2 = 0; b2 < 2; ++b2)
-                        if (inflight[b2]) mbar_wait(&st->mbar[b2], ph[b2]);
+                        if (inflight[b2] && mbar_wait(&st->mbar[b2], ph[b2], TMA_WAIT_ITERS)) ph[b2] ^= 1u;
                 }
                 __syncthreads();
+                for (int k2 = k; k2 < k_end; ++k2) abandon_column<CPT, FULL>(A, k2, jj, valid);
                 return false;
             }
             for (int i = tid; i < TL; i += NT) {  // phase 1: F0, G, F2, w

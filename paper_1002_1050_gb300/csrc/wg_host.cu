@@ -144,7 +144,8 @@ extern "C" int wigner_conv_sum_host(int l_max, int mb_max, int ms_max, int n_bet
             for (void *p : {d_c, d_b, d_a, d_beta})
                 if (p) cudaFreeAsync(p, s);
         };
-        cudaError_t e = cudaMallocFromPoolAsync(&d_beta, n_beta_b, st->pool, s);
+        cudaError_t e = wg::alloc_injected() ? cudaErrorMemoryAllocation
+                                             : cudaMallocFromPoolAsync(&d_beta, n_beta_b, st->pool, s);
         if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&d_a, n_a, st->pool, s);
         if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&d_b, n_b, st->pool, s);
         if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&d_c, n_c, st->pool, s);

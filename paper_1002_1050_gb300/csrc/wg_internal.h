@@ -24,6 +24,11 @@
 #define WG_DEVERR_BOUNDS 4
 #define WG_DEVERR_GRID 8     /* a sum over every sky order met an angle grid that is not mirror-symmetric */
 
+// tries of a bounded mbarrier wait before it gives up (each try may also suspend the
+// thread for a short hardware-chosen time); a 4 KB tile normally lands within a few
+// microseconds
+#define WG_WAIT_TRIES_DEFAULT (1 << 20)
+
 namespace wg {
 
 struct Tables;
@@ -44,6 +49,7 @@ struct ConvArgs {
     unsigned long long *counters;
     int k_lo = 0, k_hi = -1;  // chain columns k = ms (mb_max + 1) + mb in [k_lo, k_hi); k_hi < 0: all
     double offset = 0.0;      // the l_min cut's offset (kernels built with the cut only)
+    int wait_tries = WG_WAIT_TRIES_DEFAULT;  // tries of each TMA wait before it gives up
 };
 
 struct DTableBwdArgs {
@@ -65,6 +71,12 @@ struct ConvBwdArgs {
     double *grad_a, *grad_b, *grad_beta;
 };
 
+// Test hooks set through the C ABI (wigner_debug_*): whether the library's next device
+// allocation is to fail as if the device were out of memory (consumes one injected
+// failure), and the tries of each TMA wait for the launches that follow.
+bool alloc_injected();
+int wait_tries();
+
 // launchers (return cudaError_t as int)
 int launch_dtable_fp64(const DTableArgs &a, const Tables &t, void *stream);
 int launch_dtable_fp32x(const DTableArgs &a, const Tables &t, void *stream);
@@ -76,6 +88,6 @@ int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream);
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream);
 int launch_dtable_bwd(const DTableBwdArgs &a, const Tables &t, void *stream);
 int launch_conv_bwd(const ConvBwdArgs &a, const Tables &t, void *stream);
-int launch_fma_peak(int pipe, int blocks, int threads, int iters, double *sink, void *stream);
+int launch_fma_peak(int pipe, int chains, int blocks, int threads, int iters, double *sink, void *stream);
 
 }  // namespace wg

@@ -44,14 +44,19 @@ constexpr size_t kN1 = (size_t)kLcap + 1;      // 1/(l(l+1)), (l+1)/l: l <= l_ma
 constexpr size_t kWords = 4 * kN2 + 2 * kN1;
 
 static __device__ __align__(256) double g_noalloc_tables[kWords];
+// this entry point's own status word (WG_DEVERR_* bits), read and cleared by
+// wigner_noalloc_status
+static __device__ int g_noalloc_status;
 
 // Host copy of the same tables, built once per process into static storage (no heap).
 static double g_host_tables[kWords];
 static std::once_flag g_host_once;
 
 constexpr int kMaxDevices = 64;
-static double *g_dev_ptr[kMaxDevices];  // device address of g_noalloc_tables, per device
+static double *g_dev_ptr[kMaxDevices];     // device address of g_noalloc_tables, per device
+static int *g_status_ptr[kMaxDevices];     // device address of g_noalloc_status, per device
 static std::mutex g_mu;
+static const int kZero = 0;
 
 
 // Same definitions as the tables of the allocating path (Sec. 4.2.2 and Sec. 3.2):
@@ -76,9 +81,12 @@ void fill_host_tables() {
     }
 }
 
-// Set-up for the current device (first call on that device only): look up the array's
-// device address and upload the tables with a synchronous copy.
-int device_tables(double **out) {
+// Set-up for the current device (first call on that device only): look up the device
+// addresses of the array and of the status word, upload the tables, clear the word, and
+// wait for the device before publishing the addresses (a copy from pageable memory may
+// return before its transfer has landed, and the caller's stream need not be ordered
+// after the legacy stream the copies run on).
+int device_tables(double **out, int **status) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -109,15 +117,26 @@ int device_tables(double **out) {
             g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return WG_ERR_CUDA;
         }
+        int *st = nullptr;
+        e = cudaGetSymbolAddress((void **)&st, g_noalloc_status);
+        if (e != cudaSuccess || st == nullptr) {
+            g_err.code = WG_ERR_CUDA;
+            g_err = std::string("cudaGetSymbolAddress(status): ") + cudaGetErrorString(e);
+            return WG_ERR_CUDA;
+        }
         e = cudaMemcpyToSymbol(g_noalloc_tables, g_host_tables, sizeof(g_host_tables), 0, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_noalloc_status, &kZero, sizeof(int), 0, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             g_err.code = WG_ERR_CUDA;
             g_err = std::string("cudaMemcpyToSymbol: ") + cudaGetErrorString(e);
             return WG_ERR_CUDA;
         }
+        g_status_ptr[dev] = st;
         g_dev_ptr[dev] = p;
     }
     *out = g_dev_ptr[dev];
+    *status = g_status_ptr[dev];
     return WG_OK;
 }
 
@@ -144,7 +163,8 @@ extern "C" int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_
         return WG_ERR_ARG;
     }
     double *tab = nullptr;
-    int rc = device_tables(&tab);
+    int *status = nullptr;
+    int rc = device_tables(&tab, &status);
     if (rc != WG_OK) return rc;
     wg::Tables t;
     t.lnf_hi = tab;
@@ -155,9 +175,10 @@ extern "C" int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_
     t.R2 = tab + 4 * kN2 + kN1;
     t.lnf_f = t.P_f = t.Q_f = t.R1_f = t.R2_f = nullptr;  // used only by the FP32 form
     t.lcap = kLcap;
-    t.status = nullptr;  // no status word: an angle outside [0, pi] shows only as NaN outputs
+    t.status = status;  // read by wigner_noalloc_status
     wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b, (double *)c_out,
                     nullptr};
+    ca.wait_tries = wg::wait_tries();
     const int err = wg::launch_conv_fp64(ca, t, stream);
     if (err != 0) {
         g_err.code = WG_ERR_CUDA;
@@ -167,3 +188,46 @@ extern "C" int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_
     return WG_OK;
 }
 
+
+// Reads and clears this entry point's status word on the current device, after
+// synchronising `stream`.  Allocates nothing: the word is a file-scope device variable
+// read and written by symbol copies.
+extern "C" int wigner_noalloc_status(void *stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        g_err.code = WG_ERR_CUDA;
+        g_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return WG_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        g_err.code = WG_ERR_DEVICE;
+        g_err = "device ordinal beyond the supported range";
+        return WG_ERR_DEVICE;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_status_ptr[dev] == nullptr) return WG_OK;  // nothing has run on this device
+    }
+    e = cudaStreamSynchronize((cudaStream_t)stream);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&h, g_noalloc_status, sizeof(int), 0, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_noalloc_status, &kZero, sizeof(int), 0, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_err.code = WG_ERR_CUDA;
+        g_err = std::string("wigner_noalloc_status: ") + cudaGetErrorString(e);
+        return WG_ERR_CUDA;
+    }
+    if (h & WG_DEVERR_TIMEOUT) {
+        g_err.code = WG_ERR_TIMEOUT;
+        g_err = "wigner_conv_sum_noalloc: a bounded device wait gave up (the abandoned outputs are NaN)";
+        return WG_ERR_TIMEOUT;
+    }
+    if (h & WG_DEVERR_BETA) {
+        g_err.code = WG_ERR_ARG;
+        g_err = "wigner_conv_sum_noalloc: an angle was outside [0, pi] (its outputs are NaN)";
+        return WG_ERR_ARG;
+    }
+    return WG_OK;
+}

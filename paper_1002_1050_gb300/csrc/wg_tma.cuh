@@ -16,6 +16,8 @@
 #include <cuda.h>  // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
+#include "wg_internal.h"
+
 namespace wg {
 
 struct WeightMaps {
@@ -23,10 +25,10 @@ struct WeightMaps {
     CUtensorMap b;  // the beam, box {2, TL}
 };
 
-// iterations of mbarrier.try_wait before a wait gives up (each try may also suspend
-// the thread for a short hardware-chosen time); a 4 KB tile normally lands within a
-// few microseconds
-constexpr int TMA_WAIT_ITERS = 1 << 20;
+// tries of mbarrier.try_wait before a wait gives up by default; the waits of a tile
+// take their limit from the launch (ConvArgs::wait_tries), the drain of copies already
+// issued after a wait gave up always uses this one
+constexpr int TMA_WAIT_ITERS = WG_WAIT_TRIES_DEFAULT;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -55,9 +57,9 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 }
 
 // Bounded wait for the completion of the mbarrier phase of the given parity; false if
-// it has not completed after TMA_WAIT_ITERS tries.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-    for (int it = 0; it < TMA_WAIT_ITERS; ++it) {
+// it has not completed after `tries` tries (tries <= 0: gives up at once).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int tries = TMA_WAIT_ITERS) {
+    for (int it = 0; it < tries; ++it) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -74,8 +74,12 @@ def load():
                 "wigner_last_error_message": [],
                 "wigner_version": [],
                 "wigner_built_arch": [],
-                "wigner_fma_peak": [I, I, I, I, P, P, P],
+                "wigner_fma_peak": [I, I, I, I, I, P, P, P],
                 "wigner_conv_sum_noalloc": [I, I, I, I, P, P, P, P, P],
+                "wigner_noalloc_status": [P],
+                "wigner_debug_inject_alloc_failures": [I],
+                "wigner_debug_set_wait_tries": [I],
+                "wigner_debug_wait_tries": [],
                 "wigner_plan_create": [P, P],
                 "wigner_plan_destroy": [P],
                 "wigner_last_error": [],
@@ -538,13 +542,35 @@ def check_device_status(stream=None):
     _check(rc)
 
 
-def wigner_fma_peak(pipe: int, blocks: int, threads: int, iters: int, stream=None):
-    """Launch the FMA microbenchmark; returns (sink tensor, FMA lane-operations)."""
+def wigner_fma_peak(pipe: int, blocks: int, threads: int, iters: int, chains: int = 8, stream=None):
+    """Launch the FMA microbenchmark (`chains` independent FMA chains per thread); returns
+    (sink tensor, FMA lane-operations)."""
     lib = load()
     sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
     ops = ctypes.c_ulonglong(0)
-    _check(lib.wigner_fma_peak(pipe, blocks, threads, iters, _ptr(sink), ctypes.byref(ops), _stream(stream)))
+    _check(lib.wigner_fma_peak(pipe, chains, blocks, threads, iters, _ptr(sink), ctypes.byref(ops),
+                               _stream(stream)))
     return sink, int(ops.value)
+
+
+def wigner_noalloc_status(stream=None) -> int:
+    """Synchronise the stream; return (and clear) the status code of wigner_conv_sum_noalloc
+    on the current device (allocates nothing)."""
+    return int(load().wigner_noalloc_status(_stream(stream)))
+
+
+def debug_inject_alloc_failures(n: int):
+    """Test hook: the library's next n device allocations fail as if out of memory."""
+    _check(load().wigner_debug_inject_alloc_failures(int(n)))
+
+
+def debug_set_wait_tries(tries: int) -> int:
+    """Test hook: tries of each TMA wait of the fused sums launched from now on (0 gives
+    up at once; the default is 2**20).  Returns the previous value."""
+    lib = load()
+    old = int(lib.wigner_debug_wait_tries())
+    _check(lib.wigner_debug_set_wait_tries(int(tries)))
+    return old
 
 
 def exported_symbols():
@@ -555,4 +581,6 @@ def exported_symbols():
             "wigner_last_error_message", "wigner_version", "wigner_built_arch", "wigner_fma_peak",
             "wigner_conv_sum_noalloc", "wigner_batch_plan_info", "wigner_plan_create", "wigner_plan_destroy",
             "wigner_last_error", "wigner_conv_sum_host", "wigner_conv_sum_full", "wigner_data_cube",
-            "wigner_conv_sum_multi", "wigner_conv_sum_lmin", "wigner_d_matrix", "wigner_ylm"]
+            "wigner_conv_sum_multi", "wigner_conv_sum_lmin", "wigner_d_matrix", "wigner_ylm",
+            "wigner_noalloc_status", "wigner_debug_inject_alloc_failures", "wigner_debug_set_wait_tries",
+            "wigner_debug_wait_tries"]

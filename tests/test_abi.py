@@ -63,7 +63,8 @@ def test_null_and_misaligned_pointers_rejected(lib):
     assert b"aligned" in lib.wigner_last_error_message()
     assert lib.wigner_d_table(8, 2, 8, 4, FAKE, 0, None, None, None) == -1
     assert lib.wigner_d_table(8, 2, 8, 4, FAKE, 7, FAKE, None, None) == -1  # unknown form
-    assert lib.wigner_fma_peak(3, 1, 32, 1, FAKE, None, None) == -1
+    assert lib.wigner_fma_peak(3, 8, 1, 32, 1, FAKE, None, None) == -1  # unknown pipe
+    assert lib.wigner_fma_peak(0, 3, 1, 32, 1, FAKE, None, None) == -1  # chains not a power of two <= 16
 
 
 def test_empty_angle_set_is_a_noop(lib):
@@ -127,3 +128,14 @@ def test_matrix_and_ylm_validation(lib):
     assert lib.wigner_ylm(5, 6, 4, FAKE, FAKE, None) == -1
     assert lib.wigner_ylm(5, 2, 4, None, FAKE, None) == -1
     assert lib.wigner_ylm(5, 2, 0, None, None, None) == 0
+
+
+def test_debug_hooks_validate_and_round_trip(lib):
+    # host-side knobs only: no device is touched
+    assert lib.wigner_debug_inject_alloc_failures(-1) == -1
+    assert lib.wigner_debug_set_wait_tries(-5) == -1
+    old = lib.wigner_debug_wait_tries()
+    assert old == 1 << 20
+    assert lib.wigner_debug_set_wait_tries(7) == 0 and lib.wigner_debug_wait_tries() == 7
+    assert lib.wigner_debug_set_wait_tries(old) == 0 and lib.wigner_debug_wait_tries() == old
+    assert lib.wigner_debug_inject_alloc_failures(0) == 0

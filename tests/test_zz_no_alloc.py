@@ -5,11 +5,18 @@ capture in progress, an application-owned memory pool, real-time loops).  It run
 same fused FP64 kernel as wigner_conv_sum with its constant tables in a fixed array
 inside the library; the test checks two consecutive calls against wigner_conv_sum
 within the FP64 tolerance of the other parity tests (1e-11), and that the second call
-leaves the device's free memory unchanged.  This file sorts last so that a run that
-stops at the first failure has already run every other test.
+leaves the device's free memory unchanged.  Further cases: the first call of a fresh
+process made on a non-blocking stream (the set-up's table upload must be complete
+before that stream's kernel reads the tables), and the entry point's own status word
+(read by wigner_noalloc_status) for an angle out of range and for a bounded wait that
+gives up.  This file sorts last so that a run that stops at the first failure has
+already run every other test.
 """
 import ctypes
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -74,3 +81,74 @@ def test_noalloc_rejects_too_large_l_max(lib):
     rc = _call_noalloc(raw, big, 1, 1, beta, a, b, out)
     assert rc == -1
     assert b"8192" in raw.wigner_last_error_message()
+
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+_FIRST_CALL_CHILD = r"""
+import ctypes, math, sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1002_1050_gb300 import wigner as W, inputs as I
+raw = W.load()
+L, MB, MS, NB = 257, 6, 257, 517
+s = torch.cuda.Stream()  # PyTorch creates its streams non-blocking
+with torch.cuda.stream(s):
+    beta = torch.from_numpy(I.beta_gauss_legendre(NB)[0]).cuda()
+    a = torch.from_numpy(I.sky_alm(L, MS, 4)).cuda()
+    b = torch.from_numpy(I.beam_blm(L, MB, fwhm=0.04)).cuda()
+    out = torch.full((MB + 1, MS + 1, NB), complex(math.nan, math.nan), dtype=torch.complex128, device='cuda')
+    rc = raw.wigner_conv_sum_noalloc(L, MB, MS, NB, ctypes.c_void_p(beta.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                     ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(s.cuda_stream))
+s.synchronize()
+st = raw.wigner_noalloc_status(ctypes.c_void_p(s.cuda_stream))
+ref = W.wigner_conv_sum(beta, a, b)
+torch.cuda.synchronize()
+print('RESULT', rc, st, float((out - ref).abs().max()))
+"""
+
+
+def test_noalloc_first_call_on_nonblocking_stream_fresh_process():
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL_CHILD, ROOT], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [x for x in r.stdout.splitlines() if x.startswith("RESULT")][-1].split()
+    rc, st, err = int(line[1]), int(line[2]), float(line[3])
+    assert rc == 0 and st == 0
+    assert err <= TOL, err
+
+
+def test_noalloc_status_word(lib):
+    """An angle outside [0, pi] gives NaN outputs and WG_ERR_ARG from wigner_noalloc_status;
+    a wait limit of 0 tries makes every CTA give up (WG_ERR_TIMEOUT, outputs NaN); with
+    the default limit back, the call matches wigner_conv_sum again."""
+    W, raw = lib
+    L, MB, MS, NB = 150, 4, 150, 300
+    beta_h = I.beta_gauss_legendre(NB)[0]
+    beta_h[17] = 4.0
+    beta = _cuda(beta_h)
+    a = _cuda(I.sky_alm(L, MS, 8))
+    b = _cuda(I.beam_blm(L, MB, fwhm=0.05))
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert raw.wigner_noalloc_status(stream) == 0
+    out = torch.zeros((MB + 1, MS + 1, NB), dtype=torch.complex128, device="cuda")
+    assert _call_noalloc(raw, L, MB, MS, beta, a, b, out) == 0
+    assert raw.wigner_noalloc_status(stream) == -1  # WG_ERR_ARG
+    o = out.cpu().numpy()
+    assert np.all(np.isnan(o[:, :, 17])) and not np.isnan(np.delete(o, 17, axis=2)).any()
+    assert raw.wigner_noalloc_status(stream) == 0  # read and cleared
+    beta_h[17] = 0.5
+    beta = _cuda(beta_h)
+    ref = W.wigner_conv_sum(beta, a, b)
+    W.check_device_status()
+    old = W.debug_set_wait_tries(0)
+    try:
+        assert _call_noalloc(raw, L, MB, MS, beta, a, b, out) == 0
+        st = raw.wigner_noalloc_status(stream)
+    finally:
+        W.debug_set_wait_tries(old)
+    assert st == -4  # WG_ERR_TIMEOUT
+    assert bool(torch.isnan(out).all())
+    for _ in range(2):
+        assert _call_noalloc(raw, L, MB, MS, beta, a, b, out) == 0
+        assert raw.wigner_noalloc_status(stream) == 0
+        assert float((out - ref).abs().max()) <= TOL
