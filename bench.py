@@ -51,7 +51,7 @@ def _measured_fma_peak(W, stream, pipe: int):
 
     try:
         best, best_cfg = 0.0, None
-        for ch, bps in ((8, 8), (16, 8), (4, 8), (8, 4)):
+        for ch, bps in ((2, 8), (4, 8), (8, 8), (4, 4)):
             blocks = SMS * bps
             iters = (40000 if pipe == 0 else 1600000) * 8 // ch
             W.wigner_fma_peak(pipe, blocks, 256, 256, chains=ch)

@@ -245,7 +245,8 @@ int wigner_conv_sum_lmin(int l_max, int mb_max, int ms_max, int n_beta, const do
  *   b: wg_c64, shape (l_max+1, mb_max+1) if b_shared != 0 (one beam for every column),
  *      else (n_col, l_max+1, mb_max+1); 16-byte aligned.
  *   sum_cols = 0: c_out[k] holds column k, shape (n_col, mb_max+1, ms_max+1, n_beta);
- *      ceil(n_col / 4) launches.
+ *      ceil(n_col / 4) launches, or, with b_shared and n_col >= WG_MULTI_TC_MIN_COLS, the
+ *      tensor-core path of wigner_conv_sum_multi_tc.
  *   sum_cols != 0: c_out holds sum_k of the columns (the polarised total), shape
  *      (mb_max+1, ms_max+1, n_beta); the weight sum_k conj(b_k) a_k is formed per l inside
  *      the kernel, so this costs one column's work; one launch (n_col = 0 gives zeros).
@@ -257,6 +258,32 @@ int wigner_conv_sum_lmin(int l_max, int mb_max, int ms_max, int n_beta, const do
 int wigner_conv_sum_multi(int l_max, int mb_max, int ms_max, int n_beta, int n_col, const double *beta,
                           const wg_c64 *a, const wg_c64 *b, int b_shared, int sum_cols, wg_form form,
                           wg_c64 *c_out, wg_counter *counters, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * wigner_conv_sum_multi_tc -- the separate-column sum of wigner_conv_sum_multi for many
+ * skies that share one beam (the Monte-Carlo use of Sec. 4.1), on the tensor cores.
+ * wigner_conv_sum_multi routes here when sum_cols == 0, b_shared != 0 and
+ * n_col >= WG_MULTI_TC_MIN_COLS (either FP64 form).
+ *   c_out[k][mb][ms][j] = sum_l conj(b[l][mb]) a[k][l][ms] d^l_{mb,ms}(beta_j), 0 <= k < n_col.
+ *   Per chain column and 128 angles the l-sum is a real matrix product, rows = angles
+ *   (Re b_l d^l, and Im b_l d^l for beam orders whose Im b is not 0), columns = the 2 n_col
+ *   real and imaginary parts of the skies.  Each operand value is scaled into (-1, 1) by a
+ *   power of two and split exactly into six 7-bit bf16 slices; tcgen05.mma accumulates the
+ *   21 slice products of the leading levels in tensor memory (exact in FP32 for 256 orders),
+ *   folded every 256 orders into float-float accumulators.  Error per term below 2^-42
+ *   of max|a| max|b|: the FP64 path's 1e-11 bar holds (tests/ check it).  The recursion
+ *   is the FP64 two-FMA recursion of wigner_conv_sum; it runs once per 32 skies.
+ *   a: wg_c64 (n_col, l_max+1, ms_max+1); b: wg_c64 (l_max+1, mb_max+1); both 16-byte
+ *   aligned with the layouts of wigner_conv_sum_multi.  c_out overwritten.
+ *   Scratch: n_col (ms_max+1) + 2 (mb_max+1) ints from the library's stream-ordered pool
+ *   (the per-column power-of-two scales), released in stream order.
+ *   counters: [0] and [1] += the elements of the chains (counted once).
+ *   Errors: WG_ERR_ARG (sizes, NULL or misaligned pointers), WG_ERR_ALLOC, WG_ERR_CUDA;
+ *   a bounded wait that gives up: WG_ERR_TIMEOUT in the status word, outputs NaN.
+ * ------------------------------------------------------------------------- */
+#define WG_MULTI_TC_MIN_COLS 8
+int wigner_conv_sum_multi_tc(int l_max, int mb_max, int ms_max, int n_beta, int n_col, const double *beta,
+                             const wg_c64 *a, const wg_c64 *b, wg_c64 *c_out, wg_counter *counters, void *stream);
 
 /* ---------------------------------------------------------------------------
  * wigner_conv_sum_backward -- adjoint of wigner_conv_sum for a real loss L, in
@@ -396,11 +423,14 @@ int wigner_built_arch(void);
 
 /* ---------------------------------------------------------------------------
  * FMA-pipe microbenchmark (measures the roofline denominators of the path).
- *   pipe = 0: FP64 FMA, 1: FP32 FMA.  Runs `iters` iterations of `chains` (1, 2, 4, 8
- *   or 16) independent FMA chains per thread on blocks x threads (threads <= 256, a
- *   multiple of 32); writes a sink value per thread to sink (device, blocks*threads
- *   doubles) so the work cannot be elided.  Returns the number of FMA lane-operations
- *   performed in *fma_ops (host).
+ *   pipe = 0: FP64 FMA, 1: FP32 FMA.  Runs `iters` steps of `chains` (1, 2, 4, 8 or 16)
+ *   independent chains per thread on blocks x threads (threads <= 256, a multiple of
+ *   32): FP64 chains are three-term recursions x' = fma(y, x, -x_prev), the operand
+ *   pattern of the l-recursion, with every operand in a register (a DFMA that reads a
+ *   constant-bank operand does not reach the FP64 pipe's rate on GB300), FP32 chains
+ *   x = fma(x, a, b).  Writes a sink value
+ *   per thread to sink (device, blocks*threads doubles) so the work cannot be elided.
+ *   Returns the number of FMA lane-operations performed in *fma_ops (host).
  * ------------------------------------------------------------------------- */
 int wigner_fma_peak(int pipe, int chains, int blocks, int threads, int iters, double *sink,
                     unsigned long long *fma_ops, void *stream);

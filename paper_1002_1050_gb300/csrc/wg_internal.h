@@ -88,6 +88,9 @@ int launch_conv_fp64s(const ConvArgs &a, const Tables &t, void *stream);
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream);
 int launch_dtable_bwd(const DTableBwdArgs &a, const Tables &t, void *stream);
 int launch_conv_bwd(const ConvBwdArgs &a, const Tables &t, void *stream);
+int launch_conv_multi_tc(int l_max, int mb_max, int ms_max, int n_beta, int n_col, const double *beta,
+                         const double *a, const double *b, double *c_out, unsigned long long *counters,
+                         const Tables &T, int wait_tries, void *stream);
 int launch_fma_peak(int pipe, int chains, int blocks, int threads, int iters, double *sink, void *stream);
 
 }  // namespace wg

@@ -295,6 +295,9 @@ extern "C" int wigner_conv_sum_multi(int l_max, int mb_max, int ms_max, int n_be
     if (n_col > 0 && (!a || !b || !al16(a) || !al16(b)))
         return fail(WG_ERR_ARG, "a and b must be non-NULL and 16-byte aligned");
     if (counters && ((uintptr_t)counters & 7)) return fail(WG_ERR_ARG, "counters misaligned");
+    // many skies with one beam: the tensor-core path (same accuracy class)
+    if (!sum_cols && b_shared && n_col >= WG_MULTI_TC_MIN_COLS)
+        return wigner_conv_sum_multi_tc(l_max, mb_max, ms_max, n_beta, n_col, beta, a, b, c_out, counters, stream);
     wg::Tables t;
     int rc = wg::tables_for(l_max, &t);
     if (rc != WG_OK) return rc;

@@ -56,9 +56,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// wall-clock bound of every mbarrier wait, in nanoseconds: a failed try may suspend the
+// thread for a hardware-chosen time, so a count of tries alone does not bound the time a
+// wait for a phase that never completes takes
+constexpr unsigned long long WG_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded wait for the completion of the mbarrier phase of the given parity; false if
-// it has not completed after `tries` tries (tries <= 0: gives up at once).
+// it has not completed after `tries` tries or WG_WAIT_NS nanoseconds (tries <= 0: gives
+// up at once).
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int tries = TMA_WAIT_ITERS) {
+    if (tries <= 0) return false;
+    const unsigned long long t0 = globaltimer_ns();
     for (int it = 0; it < tries; ++it) {
         unsigned done;
         asm volatile(
@@ -69,6 +83,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        if (globaltimer_ns() - t0 > WG_WAIT_NS) return false;
     }
     return false;
 }

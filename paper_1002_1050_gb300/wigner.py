@@ -59,6 +59,7 @@ def load():
                 "wigner_conv_sum_host": [I, I, I, I, P, P, P, I, P, P],
                 "wigner_conv_sum_full": [I, I, I, I, P, P, P, I, P, P, P],
                 "wigner_conv_sum_multi": [I, I, I, I, I, P, P, P, I, I, I, P, P, P],
+                "wigner_conv_sum_multi_tc": [I, I, I, I, I, P, P, P, P, P, P],
                 "wigner_conv_sum_lmin": [I, I, I, I, P, P, P, I, D, I, P, P, P],
                 "wigner_d_matrix": [I, I, I, P, P, P, P],
                 "wigner_ylm": [I, I, I, P, P, P],
@@ -317,6 +318,32 @@ def wigner_conv_sum_multi(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, 
         _check(lib.wigner_conv_sum_multi(l_max, mb_max, ms_max, nb, n_col, _ptr(beta), _ptr(a), _ptr(b),
                                          int(shared), int(bool(sum_cols)), _form(form), _ptr(out), _ptr(counters),
                                          _stream(stream)))
+    return out
+
+
+def wigner_conv_sum_multi_tc(beta: torch.Tensor, a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None,
+                             counters: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """C[k][mb][ms][j] = sum_l conj(b[l][mb]) a[k][l][ms] d^l_{mb,ms}(beta_j) for many skies a[k]
+    sharing one beam b, on the tensor cores (split-bf16 slices, FP64-class accuracy).
+    a: (n_col, l_max+1, ms_max+1); b: (l_max+1, mb_max+1).  Returns (n_col, mb_max+1, ms_max+1, n_beta)."""
+    lib = load()
+    beta = _dev_tensor(beta, torch.float64, "beta")
+    a = _dev_tensor(a, torch.complex128, "a")
+    b = _dev_tensor(b, torch.complex128, "b")
+    if a.dim() != 3 or b.dim() != 2 or a.shape[1] != b.shape[0]:
+        raise ValueError("a must be a[k][l][m_sky] and b b[l][m_b] with the same number of l rows")
+    n_col, l_max, ms_max, mb_max, nb = a.shape[0], a.shape[1] - 1, a.shape[2] - 1, b.shape[1] - 1, beta.numel()
+    shape = (n_col, mb_max + 1, ms_max + 1, nb)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.complex128, device=beta.device)
+    _dev_tensor(out, torch.complex128, "out")
+    if tuple(out.shape) != shape:
+        raise ValueError("out has the wrong shape")
+    if counters is not None:
+        _dev_tensor(counters, torch.int64, "counters")
+    with torch.cuda.device(beta.device):
+        _check(lib.wigner_conv_sum_multi_tc(l_max, mb_max, ms_max, nb, n_col, _ptr(beta), _ptr(a), _ptr(b),
+                                            _ptr(out), _ptr(counters), _stream(stream)))
     return out
 
 
@@ -583,4 +610,4 @@ def exported_symbols():
             "wigner_last_error", "wigner_conv_sum_host", "wigner_conv_sum_full", "wigner_data_cube",
             "wigner_conv_sum_multi", "wigner_conv_sum_lmin", "wigner_d_matrix", "wigner_ylm",
             "wigner_noalloc_status", "wigner_debug_inject_alloc_failures", "wigner_debug_set_wait_tries",
-            "wigner_debug_wait_tries"]
+            "wigner_debug_wait_tries", "wigner_conv_sum_multi_tc"]
