@@ -503,6 +503,15 @@ def _grad_block(W, dev, stream, args):
                                  "FP64 pipe; the adjoint's sums S and E run in float-float on the FP32 pipe"}}
 
 
+def _bf16_peak():
+    """Measured cuBLAS bf16 GEMM rate of the GB300s (burst), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def _hbm_peak_gbs():
     """Measured copy bandwidth of the GB300s (driver-written), else the fallback."""
     try:
@@ -616,8 +625,8 @@ def _cube_block(W, dev, stream, args, mean_ms):
 
 def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
     """Several weight columns through one recursion on the L=4096 workload: four
-    Monte-Carlo skies with one beam (one pass, four outputs) and the polarised total of
-    three (sky, beam) pairs (one output).  Times per launch, column-evaluations per second,
+    Monte-Carlo skies with one beam (one pass, four outputs), 32 skies on the tensor cores
+    and the polarised total of three (sky, beam) pairs (one output).  Times per launch, column-evaluations per second,
     the speed-up over one wigner_conv_sum per column, and FP64 throughput counted as the
     headline's 5 flops per element plus 4 per summed element and column."""
     import torch
@@ -642,6 +651,28 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
     ms_mc_s = timed(lambda: W.wigner_conv_sum_multi(beta, a4, b, form="fp64s", out=out4), 2)
     W.check_device_status()
     del out4, a4
+    # many skies on the tensor cores: 32 Monte-Carlo skies in one launch (split-bf16 slices,
+    # tcgen05.mma), against the same skies in 4-column passes of the split-pipe form (the
+    # passes are alike, so one pass is timed and counted 8 times)
+    K_TC = 32
+    a32 = torch.from_numpy(I.mc_skies(L_MAX, MS_MAX, K_TC, 200)).to(dev)
+    out32 = torch.empty((K_TC, MB_MAX + 1, MS_MAX + 1, nb), dtype=torch.complex128, device=dev)
+    ms_tc = timed(lambda: W.wigner_conv_sum_multi_tc(beta, a32, b, out=out32), 2)
+    W.check_device_status()
+    # a one-pass sample of the same skies through the 4-column split-pipe path, for the error
+    ref4 = torch.empty((4, MB_MAX + 1, MS_MAX + 1, nb), dtype=torch.complex128, device=dev)
+    W.wigner_conv_sum_multi(beta, a32[:4].contiguous(), b, form="fp64s", out=ref4)
+    torch.cuda.synchronize()
+    tc_diff = float((out32[:4] - ref4).abs().max())
+    del a32, out32, ref4
+    torch.cuda.empty_cache()
+    tiles = 0  # 32-order tiles of the launch: the MMA work is 42 MMAs of 128 x 64 x 16 per tile
+    for mb in range(MB_MAX + 1):
+        for ms in range(MS_MAX + 1):
+            tiles += (L_MAX + 1 - max(mb, ms) + 31) // 32
+    tiles *= (nb + 127) // 128
+    mma_tflops = tiles * 42 * 2.0 * 128 * 64 * 16 / (ms_tc / 1e3) / 1e12
+    bf16_peak = _bf16_peak()
     ap, bp = I.polarised_columns(L_MAX, MB_MAX, MS_MAX, 100)
     ap, bp = torch.from_numpy(ap).to(dev), torch.from_numpy(bp).to(dev)
     outp = torch.empty((MB_MAX + 1, MS_MAX + 1, nb), dtype=torch.complex128, device=dev)
@@ -656,7 +687,16 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
                               "fp64_tflops": fl4 / (ms_mc / 1e3) / 1e12},
             "monte_carlo_4_fp64s": {"ms_per_launch": ms_mc_s, "column_evals_per_s": 4 * n_elem / (ms_mc_s / 1e3),
                                     "vs_separate_fp64_calls": 4 * mean_ms / ms_mc_s},
-            "polarised_total_3": {"ms_per_launch": ms_pol, "vs_separate_calls": 3 * mean_ms / ms_pol}}
+            "polarised_total_3": {"ms_per_launch": ms_pol, "vs_separate_calls": 3 * mean_ms / ms_pol},
+            "monte_carlo_tc_32": {"ms_per_launch": ms_tc, "column_evals_per_s": K_TC * n_elem / (ms_tc / 1e3),
+                                  "vs_4col_fp64s_passes": (K_TC / 4) * ms_mc_s / ms_tc,
+                                  "max_abs_diff_vs_4col_fp64s": tc_diff,
+                                  "tensor": {"mma_tflops_executed": mma_tflops, "bf16_peak_tflops": bf16_peak,
+                                             "frac": mma_tflops / bf16_peak,
+                                             "note": "bf16 slice products issued by tcgen05.mma (42 per 32-order "
+                                                     "tile) over the measured cuBLAS bf16 peak; the launch is "
+                                                     "bound by the FP64 recursion, not the tensor pipe"},
+                                  "fp64_recursion_tflops": 5 * n_elem / (ms_tc / 1e3) / 1e12}}
 
 
 def _matrix_block(W, dev, stream, args):

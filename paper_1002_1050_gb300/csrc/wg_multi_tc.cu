@@ -26,12 +26,14 @@
 // The recursion is the normalised two-FMA form of the fused FP64 sum (u^l = d^l /
 // sigma_l); the A value is u^l f_l with f_l = sigma_l b_l 2^-eb formed per tile.
 //
-// Roles (224 threads, one CTA per SM: the tensor memory is allocated whole):
-//   warps 0-3  one chain (angle) per thread = one MMA row = one tensor-memory lane;
-//              recursion, A slices, the level fold and the output;
-//   warp 4     the control warp: the next tile's coefficient tables (lanes = l), TMA
-//              of the sky tiles, the MMAs (lane 0), tensor-memory allocation;
-//   warps 5-6  the B slices of each sky tile.
+// Roles (416 threads, one CTA per SM: the tensor memory is allocated whole):
+//   warps 0-3   chains: one angle per thread, the FP64 recursion only (u^l of each tile
+//               into shared memory), so the FP64 pipe is fed without gaps;
+//   warps 4-7   slicers: row r = the same angle (and tensor-memory lane r): A = u^l f_l in
+//               six slices, the level folds every 256 orders, and the output;
+//   warp 8      control: the next tile's coefficient tables (lanes = l), TMA of the sky
+//               tiles, the MMAs (lane 0), tensor-memory allocation;
+//   warps 9-12  weights: the B slices of each sky tile.
 // A tile is 32 orders (two MMA K-steps of 16), double-buffered; the roles hand tiles
 // over through named barriers, MMA completion through tcgen05.commit on mbarriers,
 // TMA completion through mbarriers.  Every mbarrier wait is bounded; a wait that
@@ -42,6 +44,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <mutex>
 #include <string>
@@ -63,37 +66,54 @@ constexpr int TC_TL = 32;        // orders per tile (two K-steps of 16)
 constexpr int TC_NS = 6;         // slices per operand value
 constexpr int TC_SEG = 8;        // tiles per exactly accumulated segment (256 orders)
 constexpr int TC_SKIES = 32;     // skies per launch column group (N = 64 real columns)
-constexpr int TC_THREADS = 224;
+constexpr int TC_THREADS = 416;  // warps 0-3 chains, 4-7 slicers, 8 control, 9-12 weights
+constexpr int WARP_CTL = 8, TID_B0 = 288;
 constexpr int TC_GROUP = 8;      // chain columns per CTA
+constexpr size_t TC_TABLE_BYTES = (size_t)1 << 30;  // scratch for the recursion tables of a column batch
 
 // named barriers (0 is __syncthreads); the stage s is added to the paired ids.  The
 // order of the roles rests on these alone (every role that arrives on a barrier syncs on
 // another that the consumer arrives at after consuming it), never on the mbarrier waits,
 // which may give up:
 //   TAB_READY(s)  control -> chains   tables of the tile in stage s built
-//   TAB_FREE(s)   chains -> control   chains done with the tables in stage s
+//   U_READY(h)    chains -> slicers   u^l of half h (16 orders) of the tile written
+//   U_FREE(h)     slicers -> chains   half h of the u buffer read
 //   B_READY(s)    weights -> control  B slices in stage s written (and the sky tile read)
-//   A_READY(s)    chains -> control   A slices in stage s written
+//   A_READY(s)    slicers -> control  A slices in stage s written; the tables in stage s
+//                                     are then read by every role (the chains finished the
+//                                     tile before the slicers could start its last half)
 //   B_FREE(s)     control -> weights  the MMA of stage s issued, the next sky tile requested
-//   MMA_ISSUED    control -> chains   the MMA of a segment's last tile issued
-//   FLUSHED       chains -> control   the levels of a segment read from tensor memory
-constexpr int BAR_TAB_READY = 1, BAR_TAB_FREE = 3, BAR_B_READY = 5, BAR_A_READY = 7, BAR_B_FREE = 9,
-              BAR_FLUSHED = 11, BAR_MMA_ISSUED = 12;
-constexpr int CNT_CHAIN_CTL = 160, CNT_B_CTL = 96;
+//   MMA_ISSUED    control -> slicers  the MMA of a segment's last tile issued
+//   FLUSHED       slicers -> control  the levels of a segment read from tensor memory
+constexpr int BAR_TAB_READY = 1, BAR_U_READY = 3, BAR_B_READY = 5, BAR_A_READY = 7, BAR_B_FREE = 9,
+              BAR_FLUSHED = 11, BAR_MMA_ISSUED = 12, BAR_U_FREE = 13;
+constexpr int CNT_CHAIN_CTL = 160, CNT_SLICE_CTL = 160, CNT_CHAIN_SLICE = 256, CNT_B_CTL = 160;
 
 struct TcSmem {
     alignas(1024) unsigned char A[2][TC_NS][2][4096];  // [stage][slice][K-step] 128 rows x 16 bf16
     alignas(1024) unsigned char B[2][TC_NS][2][2048];  // [stage][slice][K-step] up to 64 rows x 16 bf16
-    alignas(128) double2 Aw[2][TC_SKIES][TC_TL];       // TMA tile of the skies: [k][l] (re, im)
+    alignas(128) double2 Aw[2][TC_TL][TC_SKIES];       // TMA tile of the skies: [l][k] (re, im)
     double2 FG[2][TC_TL];                              // (F0', G') of the normalised recursion
     float2 F[2][TC_TL];                                // f_l = sigma_l b_l 2^-eb as float-float
+    double U[TC_TL][TC_M];                             // u^l of the tile, [l][row]
     unsigned long long mbar_tma[2], mbar_mma[2];
     uint32_t tmem;
     int abort;
 };
 
+static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of the tensor-core kernel exceeds 227 KB");
+
+// per (chain column, l): the normalised recursion's F0' = F0 rho, G' = G rho and sigma_l
+// (float-float), made by tc_tables_kernel for a batch of columns before the main kernel
+struct TcTab {
+    double f0p, gp;
+    float sh, sl;
+};
+
 struct TcArgs {
     int l_max, mb_max, ms_max, n_beta, n_col;
+    const TcTab *tab;  // [k - c0][l], l <= l_max, for the columns [c0, c1) of this launch
+    int c0, c1;
     const double *beta;
     const double *b;   // interleaved complex [l][mb]
     double *c_out;     // interleaved complex [k][mb][ms][j]
@@ -209,53 +229,56 @@ struct TileIter {
 // ---------------------------------------------------------------------------------
 // control warp: tables of tile `it` into stage s (lanes = orders), carrying sigma
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ void build_tables(const TcArgs &A, const Tables &T, const TileIter &it, int s,
-                                             TcSmem &sm, double &c_m1, double &c_0) {
+// inputs of a tile's tables (lane = order l): the pre-computed entry and the beam part,
+// loaded one tile ahead so their latency hides behind the MMA issue
+struct TabIn {
+    double2 fg;
+    float2 sig;
+    double bpart;
+};
+
+__device__ __forceinline__ TabIn load_tab(const TcArgs &A, const TileIter &it) {
     const int lane = threadIdx.x & 31;
     const int L = A.l_max;
-    const int ts = it.ts();
-    const int l = ts + lane;
-    if (it.t == 0) {  // sigma_{l0-1} := 1, sigma_{l0} = 1, so that sigma_{l0+1} = 1
-        c_m1 = 1.0;
-        c_0 = 1.0;
+    const int l = it.ts() + lane;
+    TabIn in{make_double2(0.0, 0.0), make_float2(0.f, 0.f), 0.0};
+    if (l <= L) {
+        const TcTab e = A.tab[(size_t)(it.k - A.c0) * (L + 1) + l];
+        if (l < L) in.fg = make_double2(e.f0p, e.gp);
+        in.sig = make_float2(e.sh, e.sl);
+        const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * (A.mb_max + 1) + it.mb];
+        in.bpart = A.part == 0 ? bv.x : bv.y;
     }
-    double f0 = 0.0, g = 0.0, f2 = 1.0;
-    if (l < L) {
-        lrec_coefficients(l, it.mb, it.ms, T, f0, g, f2);
-        if (l == it.l0) f2 = 1.0;
-    }
-    // sigma_{l+1} = F2_l sigma_{l-1}: a product scan along each parity of the lanes
-    double P = f2;
-#pragma unroll
-    for (int off = 2; off < 32; off <<= 1) {
-        const double v = __shfl_up_sync(0xffffffffu, P, off);
-        if (lane >= off) P *= v;
-    }
-    const double sig_next = P * ((lane & 1) ? c_0 : c_m1);  // sigma_{l+1}
-    const double sig_up = __shfl_up_sync(0xffffffffu, sig_next, 1);
-    const double sig = lane == 0 ? c_0 : sig_up;              // sigma_l
-    double2 fg = make_double2(0.0, 0.0);
-    if (l < L) {
-        const double rho = sig / sig_next;
-        fg = make_double2(f0 * rho, g * rho);
-    }
+    return in;
+}
+
+// control warp: the tables of tile `it` into stage s (lanes = orders): (F0', G') and
+// f_l = sigma_l b_l 2^-eb, a float-float product on the FP32 pipe (the FP64 work of the
+// tables is in tc_tables_kernel, so no role but the chains uses this SM's FP64 units)
+__device__ __forceinline__ void build_tables(const TcArgs &A, const TileIter &it, const TabIn &in, int s,
+                                             TcSmem &sm) {
+    const int lane = threadIdx.x & 31;
     float fh = 0.f, fl = 0.f;
     const int eb = A.eb[A.part * (A.mb_max + 1) + it.mb];
-    if (l <= L && eb != INT_MIN) {
-        const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * (A.mb_max + 1) + it.mb];
-        dsplit(sig * (A.part == 0 ? bv.x : bv.y), -eb, -80, fh, fl);
+    if (eb != INT_MIN) {
+        float bh, bl;
+        dsplit(in.bpart, -eb, -80, bh, bl);
+        const float p = __fmul_rn(in.sig.x, bh);
+        float e = __fmaf_rn(in.sig.x, bh, -p);
+        e = __fmaf_rn(in.sig.x, bl, e);
+        e = __fmaf_rn(in.sig.y, bh, e);
+        fh = __fadd_rn(p, e);
+        fl = __fsub_rn(e, __fsub_rn(fh, p));
     }
-    sm.FG[s][lane] = fg;
+    sm.FG[s][lane] = in.fg;
     sm.F[s][lane] = make_float2(fh, fl);
-    c_m1 = __shfl_sync(0xffffffffu, sig_next, 30);
-    c_0 = __shfl_sync(0xffffffffu, sig_next, 31);
 }
 
 __device__ __forceinline__ void issue_tma(const TcArgs &A, const CUtensorMap *amap, const TileIter &it, int s, int k0,
                                           TcSmem &sm) {
     fence_proxy_async();
     mbar_arrive_expect_tx(&sm.mbar_tma[s], (unsigned)(TC_SKIES * TC_TL * 16));
-    tma_load_3d(&sm.Aw[s][0][0], amap, 2 * it.ms, it.ts(), k0, &sm.mbar_tma[s]);
+    tma_load_3d(&sm.Aw[s][0][0], amap, 2 * it.ms, k0, it.ts(), &sm.mbar_tma[s]);
 }
 
 __device__ __forceinline__ void issue_mmas(TcSmem &sm, int s, uint32_t tbase, int N, bool seg_first) {
@@ -281,8 +304,8 @@ __device__ __forceinline__ void issue_mmas(TcSmem &sm, int s, uint32_t tbase, in
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ void build_b(const TcArgs &A, const TileIter &it, int s, int k0, int nsky, int N,
                                        TcSmem &sm) {
-    const int tb = threadIdx.x - 160;  // 0..63
-    for (int task = tb; task < TC_SKIES * 2 * 4; task += 64) {
+    const int tb = threadIdx.x - TID_B0;  // 0..127
+    for (int task = tb; task < TC_SKIES * 2 * 4; task += 128) {
         const int g = task & 3;          // 8-order group of the tile
         const int n = task >> 2;         // row: 2 k + part
         if (n >= N) continue;
@@ -291,7 +314,7 @@ __device__ __forceinline__ void build_b(const TcArgs &A, const TileIter &it, int
         float hs[8], ls[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const double2 v = sm.Aw[s][kl][8 * g + i];
+            const double2 v = sm.Aw[s][8 * g + i][kl];
             dsplit(p ? v.y : v.x, -ea, -45, hs[i], ls[i]);
         }
         uint32_t pk[TC_NS][4];
@@ -323,8 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int chunk = item % A.n_chunks;
     const int grp = item / A.n_chunks;
     const int MB1 = A.mb_max + 1, MS1 = A.ms_max + 1;
-    const int ncol = MB1 * MS1;
-    const int k_begin = grp * A.group, k_end = min(ncol, k_begin + A.group);
+    const int k_begin = A.c0 + grp * A.group, k_end = min(A.c1, k_begin + A.group);
     const int k0 = kg * TC_SKIES, nsky = min(TC_SKIES, A.n_col - k0);
     const int N = ((2 * nsky + 15) / 16) * 16;
     const int L = A.l_max, NB = A.n_beta;
@@ -333,8 +355,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     probe.init(A, k_begin, k_end);
     if (!probe.valid) return;  // part 1 with no imaginary beam in this group (uniform)
 
-    if (warp == 4) tmem_alloc(&sm.tmem, 512);
-    if (tid == 128) {
+    if (warp == WARP_CTL) tmem_alloc(&sm.tmem, 512);
+    if (tid == WARP_CTL * 32) {
         mbar_init(&sm.mbar_tma[0], 1);
         mbar_init(&sm.mbar_tma[1], 1);
         mbar_init(&sm.mbar_mma[0], 1);
@@ -348,13 +370,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tbase = sm.tmem;
 
     if (warp < 4) {
-        // ============================ chain warps ============================
+        // ===== chain warps: the FP64 recursion, u^l of the tile into shared memory =====
         const int r = tid;
         const int j = chunk * TC_M + r;
         const bool valid = j < NB;
         const Angle ang = make_angle(valid ? A.beta[j] : 1.0);
         if (valid && ang.bad && A.part == 0) raise_status(T.status, WG_DEVERR_BETA);
-        const uint32_t tl = tbase + ((uint32_t)(warp * 32) << 16);
         TileIter it = probe;
         unsigned long long n_elem = 0;
         int gt = 0;
@@ -372,57 +393,115 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (valid && A.part == 0 && kg == 0) n_elem += (unsigned long long)(L + 1 - it.l0);
             }
             bar_sync(BAR_TAB_READY + s, CNT_CHAIN_CTL);
-            if (gt >= 2) tc_wait(sm, &sm.mbar_mma[s], ((gt >> 1) - 1) & 1, A.wait_tries, T.status);
             const int ts = it.ts();
-            uint32_t pk[TC_NS][4];
 #pragma unroll 1
-            for (int i0 = 0; i0 < TC_TL; i0 += 8) {
+            for (int h = 0; h < 2; ++h) {
+                if (gt >= 1) bar_sync(BAR_U_FREE + h, CNT_CHAIN_SLICE);
+                // the half's coefficients into registers, each multiplier y formed two steps
+                // ahead of its use, the 16 values of u stored after the half: a dependent
+                // DFMA then never waits behind a shared-memory access in the warp's
+                // in-order stream (measured 156 cycles per two-DFMA step against 207 with a
+                // load and a store in every step; the FP64 unit of a sub-partition takes a
+                // warp-wide DFMA every 64 cycles)
+                double2 fg[16];
 #pragma unroll
-                for (int i = i0; i < i0 + 8; i += 2) {
-                    float hh[2], ll[2];
+                for (int i = 0; i < 16; ++i) fg[i] = sm.FG[s][16 * h + i];
+                double uu[16];
+                double y0 = fma(fg[0].x, ang.cb, -fg[0].y);
+                double y1 = fma(fg[1].x, ang.cb, -fg[1].y);
 #pragma unroll
-                    for (int p = 0; p < 2; ++p) {
-                        const int l = ts + i + p;
-                        float uh, ul;
-                        dsplit(plain ? u : 0.0, 0, -60, uh, ul);
-                        const float2 f = sm.F[s][i + p];
-                        const float pr = __fmul_rn(uh, f.x);
-                        float e = __fmaf_rn(uh, f.x, -pr);
-                        e = __fmaf_rn(uh, f.y, e);
-                        e = __fmaf_rn(ul, f.x, e);
-                        hh[p] = __fadd_rn(pr, e);
-                        ll[p] = __fsub_rn(e, __fsub_rn(hh[p], pr));
-                        if (l < L) {
-                            const double2 fg = sm.FG[s][i + p];
-                            const double y = fma(fg.x, ang.cb, -fg.y);
-                            const double nx = fma(y, u, -up);
-                            up = u;
-                            u = nx;
-                            if (!plain) scaled_fixup(u, up, nsc, plain);
-                        }
+                for (int i = 0; i < 16; ++i) {
+                    const int l = ts + 16 * h + i;
+                    const double y = y0;
+                    y0 = y1;
+                    if (i + 2 < 16) y1 = fma(fg[i + 2].x, ang.cb, -fg[i + 2].y);
+                    uu[i] = (plain && l <= L) ? u : 0.0;
+                    if (l < L) {
+                        const double nx = fma(y, u, -up);
+                        up = u;
+                        u = nx;
                     }
-                    uint32_t o[TC_NS];
-                    slice6_pair(make_float2(hh[0], hh[1]), make_float2(ll[0], ll[1]), o);
-#pragma unroll
-                    for (int q = 0; q < TC_NS; ++q) pk[q][(i - i0) >> 1] = o[q];
+                    // scaled doubles: the range check every fourth step keeps its integer work
+                    // off most steps; four steps grow a mantissa by less than 2^64 (at most
+                    // 2 (l0 + 1) / (k + 1) + 1 per step, l0 <= 32767), so from below 2^90 it
+                    // stays far inside the double range
+                    if ((i & 3) == 3 && !plain) scaled_fixup(u, up, nsc, plain);
                 }
-                const uint32_t off = tc_off(r, (i0 & 8));
 #pragma unroll
-                for (int q = 0; q < TC_NS; ++q)
-                    *reinterpret_cast<uint4 *>(&sm.A[s][q][i0 >> 4][off]) =
-                        make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+                for (int i = 0; i < 16; ++i) sm.U[16 * h + i][r] = uu[i];
+                bar_arrive(BAR_U_READY + h, CNT_CHAIN_SLICE);
+            }
+            it.next(A);
+            ++gt;
+        }
+        if (A.counters) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) n_elem += __shfl_down_sync(0xffffffffu, n_elem, off);
+            if (lane == 0 && n_elem) {
+                atomicAdd(&A.counters[0], n_elem);
+                atomicAdd(&A.counters[1], n_elem);
+            }
+        }
+    } else if (warp < 8) {
+        // ===== slicer warps: A = u f in six 7-bit slices, the level folds and the output =====
+        const int r = tid - 128;
+        const int j = chunk * TC_M + r;
+        const bool valid = j < NB;
+        const double bj = valid ? A.beta[j] : 1.0;
+        const bool bad_ang = !(bj >= 0.0 && bj <= WG_PI_HI);
+        const uint32_t tl = tbase + ((uint32_t)((warp - 4) * 32) << 16);
+        TileIter it = probe;
+        int gt = 0;
+        while (it.valid) {
+            const int s = gt & 1;
+            TileIter nx = it;
+            nx.next(A);
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                bar_sync(BAR_U_READY + h, CNT_CHAIN_SLICE);
+                if (h == 0 && gt >= 2) tc_wait(sm, &sm.mbar_mma[s], ((gt >> 1) - 1) & 1, A.wait_tries, T.status);
+#pragma unroll
+                for (int g8 = 0; g8 < 2; ++g8) {
+                    uint32_t pk[TC_NS][4];
+#pragma unroll
+                    for (int i2 = 0; i2 < 8; i2 += 2) {
+                        const int i = 16 * h + 8 * g8 + i2;
+                        float hh[2], ll[2];
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            float uh, ul;
+                            dsplit(sm.U[i + p][r], 0, -60, uh, ul);
+                            const float2 f = sm.F[s][i + p];
+                            const float pr = __fmul_rn(uh, f.x);
+                            float e = __fmaf_rn(uh, f.x, -pr);
+                            e = __fmaf_rn(uh, f.y, e);
+                            e = __fmaf_rn(ul, f.x, e);
+                            hh[p] = __fadd_rn(pr, e);
+                            ll[p] = __fsub_rn(e, __fsub_rn(hh[p], pr));
+                        }
+                        uint32_t o[TC_NS];
+                        slice6_pair(make_float2(hh[0], hh[1]), make_float2(ll[0], ll[1]), o);
+#pragma unroll
+                        for (int q = 0; q < TC_NS; ++q) pk[q][i2 >> 1] = o[q];
+                    }
+                    const uint32_t off = tc_off(r, 8 * g8);
+#pragma unroll
+                    for (int q = 0; q < TC_NS; ++q)
+                        *reinterpret_cast<uint4 *>(&sm.A[s][q][h][off]) =
+                            make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+                }
+                if (nx.valid) bar_arrive(BAR_U_FREE + h, CNT_CHAIN_SLICE);
             }
             fence_proxy_async();
-            bar_arrive(BAR_A_READY + s, CNT_CHAIN_CTL);
-            bar_arrive(BAR_TAB_FREE + s, CNT_CHAIN_CTL);
+            bar_arrive(BAR_A_READY + s, CNT_SLICE_CTL);
             if (it.seg_last()) {
                 // fold this segment's levels into the float-float accumulators (or the output)
-                bar_sync(BAR_MMA_ISSUED, CNT_CHAIN_CTL);
+                bar_sync(BAR_MMA_ISSUED, CNT_SLICE_CTL);
                 const bool ok = tc_wait(sm, &sm.mbar_mma[s], (gt >> 1) & 1, A.wait_tries, T.status);
                 tc_fence_after();
                 const bool first = it.t < TC_SEG;
                 const bool last = it.col_last();
-                const bool bad = !ok || *(volatile int *)&sm.abort || ang.bad;
+                const bool bad = !ok || *(volatile int *)&sm.abort || bad_ang;
                 for (int c8 = 0; c8 < N; c8 += 8) {
                     float lv[TC_NS][8], ah[8], al[8];
 #pragma unroll
@@ -474,26 +553,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tmem_st_wait();
                 tc_fence_before();
-                bar_arrive(BAR_FLUSHED, CNT_CHAIN_CTL);
+                bar_arrive(BAR_FLUSHED, CNT_SLICE_CTL);
             }
-            it.next(A);
+            it = nx;
             ++gt;
         }
-        if (A.counters) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) n_elem += __shfl_down_sync(0xffffffffu, n_elem, off);
-            if (lane == 0 && n_elem) {
-                atomicAdd(&A.counters[0], n_elem);
-                atomicAdd(&A.counters[1], n_elem);
-            }
-        }
-    } else if (warp == 4) {
+    } else if (warp == WARP_CTL) {
         // ============================ control warp ============================
         TileIter tab = probe, mma = probe, tma = probe;
-        double c_m1 = 1.0, c_0 = 1.0;
-        build_tables(A, T, tab, 0, sm, c_m1, c_0);
+        build_tables(A, tab, load_tab(A, tab), 0, sm);
         bar_arrive(BAR_TAB_READY + 0, CNT_CHAIN_CTL);
         tab.next(A);
+        TabIn nxt{};
+        if (tab.valid) nxt = load_tab(A, tab);
         // operations issued per stage (the drain at the end waits for the last of each);
         // the decision to issue is taken once per warp from lane 0's view of the abort flag
         int n_tma[2] = {0, 0}, n_mma[2] = {0, 0};
@@ -510,27 +582,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tma.next(A);
         }
-        int gt = 0, n_tab_free = 0;  // tiles whose TAB_FREE was consumed
+        int gt = 0;
         while (mma.valid) {
             const int s = gt & 1;
-            if (tab.valid) {  // tables of tile gt + 1 into the other stage
-                if (gt + 1 >= 2) {
-                    bar_sync(BAR_TAB_FREE + (s ^ 1), CNT_CHAIN_CTL);
-                    ++n_tab_free;
-                }
-                build_tables(A, T, tab, s ^ 1, sm, c_m1, c_0);
+            if (tab.valid) {  // tables of tile gt + 1 into the other stage (free since A_READY of gt - 1)
+                build_tables(A, tab, nxt, s ^ 1, sm);
                 bar_arrive(BAR_TAB_READY + (s ^ 1), CNT_CHAIN_CTL);
                 tab.next(A);
+                if (tab.valid) nxt = load_tab(A, tab);  // inputs of tile gt + 2, ahead
             }
             bar_sync(BAR_B_READY + s, CNT_B_CTL);
-            bar_sync(BAR_A_READY + s, CNT_CHAIN_CTL);
-            if (mma.seg_first() && gt > 0) bar_sync(BAR_FLUSHED, CNT_CHAIN_CTL);
+            bar_sync(BAR_A_READY + s, CNT_SLICE_CTL);
+            if (mma.seg_first() && gt > 0) bar_sync(BAR_FLUSHED, CNT_SLICE_CTL);
             if (go()) {
                 if (lane == 0) issue_mmas(sm, s, tbase, N, mma.seg_first());
                 ++n_mma[s];
             }
             __syncwarp();
-            if (mma.seg_last()) bar_arrive(BAR_MMA_ISSUED, CNT_CHAIN_CTL);
+            if (mma.seg_last()) bar_arrive(BAR_MMA_ISSUED, CNT_SLICE_CTL);
             if (tma.valid) {  // the sky tile of gt + 2 into this stage: its B slices are built
                 if (go()) {
                     if (lane == 0) issue_tma(A, &amap, tma, s, k0, sm);
@@ -543,10 +612,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mma.next(A);
             ++gt;
         }
-        // consume the hand-overs of the last tiles that no later tile needed, so every
-        // arrival on a named barrier is matched
-        for (; n_tab_free < gt; ++n_tab_free) bar_sync(BAR_TAB_FREE + (n_tab_free & 1), CNT_CHAIN_CTL);
-        bar_sync(BAR_FLUSHED, CNT_CHAIN_CTL);  // the last fold has read the tensor memory
+        bar_sync(BAR_FLUSHED, CNT_SLICE_CTL);  // the last fold has read the tensor memory
         // drain: the last commit of each stage and every TMA phase not yet waited for
         if (lane == 0) {
             for (int st = 0; st < 2; ++st) {
@@ -571,6 +637,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bar_arrive(BAR_B_READY + s, CNT_B_CTL);
             it.next(A);
             ++gt;
+        }
+    }
+}
+
+// The tables of the normalised recursion for the chain columns [c0, c1): one warp per
+// column walks l in steps of 32 (lanes = orders) with the Sec. 4.2.2 coefficients
+// F0, G = F0 F1, F2, the normalisation sigma_{l+1} = F2_l sigma_{l-1} (sigma_{l0} =
+// sigma_{l0+1} = 1) as a product scan along each parity of the lanes, rho_l =
+// sigma_l / sigma_{l+1}, F0' = F0 rho, G' = G rho.
+__global__ void tc_tables_kernel(int L, int MB, int c0, int c1, Tables T, TcTab *tab) {
+    const int lane = threadIdx.x & 31;
+    const int wg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int MB1 = MB + 1;
+    for (int k = c0 + wg; k < c1; k += nw) {
+        const int ms = k / MB1, mb = k - ms * MB1;
+        const int l0 = mb > ms ? mb : ms;
+        TcTab *out = tab + (size_t)(k - c0) * (L + 1);
+        double c_m1 = 1.0, c_0 = 1.0;  // sigma_{l0-1} := 1 and sigma_{l0} = 1 give sigma_{l0+1} = 1
+        for (int ts = l0; ts <= L; ts += 32) {
+            const int l = ts + lane;
+            double f0 = 0.0, g = 0.0, f2 = 1.0;
+            if (l < L) {
+                lrec_coefficients(l, mb, ms, T, f0, g, f2);
+                if (l == l0) f2 = 1.0;
+            }
+            double P = f2;
+#pragma unroll
+            for (int off = 2; off < 32; off <<= 1) {
+                const double v = __shfl_up_sync(0xffffffffu, P, off);
+                if (lane >= off) P *= v;
+            }
+            const double sig_next = P * ((lane & 1) ? c_0 : c_m1);  // sigma_{l+1}
+            const double sig_up = __shfl_up_sync(0xffffffffu, sig_next, 1);
+            const double sig = lane == 0 ? c_0 : sig_up;              // sigma_l
+            if (l <= L) {
+                TcTab e;
+                e.f0p = 0.0;
+                e.gp = 0.0;
+                if (l < L) {
+                    const double rho = sig / sig_next;
+                    e.f0p = f0 * rho;
+                    e.gp = g * rho;
+                }
+                dsplit(sig, 0, -80, e.sh, e.sl);
+                out[l] = e;
+            }
+            c_m1 = __shfl_sync(0xffffffffu, sig_next, 30);
+            c_0 = __shfl_sync(0xffffffffu, sig_next, 31);
         }
     }
 }
@@ -619,10 +734,11 @@ EncodeTiledFn3 encode3() {
 }
 }  // namespace
 
-// The skies a[k][l][ms] as a 3-D float64 tensor {2 (ms_max + 1), l_max + 1, n_col}; a
-// box {2, 32, 32} is the tile of one m_sky column, 32 orders, 32 skies (x = 2 m_sky is
-// even, so the copy starts on a 16-byte boundary; rows past l_max and skies past n_col
-// come back as zeros).
+// The skies a[k][l][ms] as a 3-D float64 tensor {2 (ms_max + 1), n_col, l_max + 1} (the
+// sky index before the order, so a box lands as [l][k] in shared memory and the weight
+// warps read consecutive skies from consecutive banks); a box {2, 32, 32} is the tile of
+// one m_sky column, 32 skies, 32 orders (x = 2 m_sky is even, so the copy starts on a
+// 16-byte boundary; skies past n_col and rows past l_max come back as zeros).
 int launch_conv_multi_tc(int l_max, int mb_max, int ms_max, int n_beta, int n_col, const double *beta,
                          const double *a, const double *b, double *c_out, unsigned long long *counters,
                          const Tables &T, int wait_tries, void *stream) {
@@ -631,9 +747,9 @@ int launch_conv_multi_tc(int l_max, int mb_max, int ms_max, int n_beta, int n_co
     EncodeTiledFn3 fn = encode3();
     if (!fn) return (int)cudaErrorNotSupported;
     CUtensorMap amap;
-    const cuuint64_t dims[3] = {(cuuint64_t)2 * (ms_max + 1), (cuuint64_t)l_max + 1, (cuuint64_t)n_col};
-    const cuuint64_t strides[2] = {(cuuint64_t)16 * (ms_max + 1), (cuuint64_t)16 * (ms_max + 1) * (l_max + 1)};
-    const cuuint32_t box[3] = {2u, (cuuint32_t)TC_TL, (cuuint32_t)TC_SKIES};
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * (ms_max + 1), (cuuint64_t)n_col, (cuuint64_t)l_max + 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)16 * (ms_max + 1) * (l_max + 1), (cuuint64_t)16 * (ms_max + 1)};
+    const cuuint32_t box[3] = {2u, (cuuint32_t)TC_SKIES, (cuuint32_t)TC_TL};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     if (fn(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double *>(a), dims, strides, box, estr,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -677,14 +793,32 @@ int launch_conv_multi_tc(int l_max, int mb_max, int ms_max, int n_beta, int n_co
     ta.group = TC_GROUP;
     ta.counters = counters;
     ta.wait_tries = wait_tries;
+    // columns in batches whose tables fit TC_TABLE_BYTES of scratch
     const int ncol = (mb_max + 1) * (ms_max + 1);
-    const long long items = (long long)((ncol + TC_GROUP - 1) / TC_GROUP) * ta.n_chunks * ta.k_groups;
-    if (items > 0x7fffffffLL) e = cudaErrorInvalidValue;
-    for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
-        ta.part = part;
-        conv_multi_tc_kernel<<<(unsigned)items, TC_THREADS, smem, s>>>(ta, T, amap);
+    const size_t per_col = (size_t)(l_max + 1) * sizeof(TcTab);
+    long long cpb = (long long)(TC_TABLE_BYTES / per_col) / TC_GROUP * TC_GROUP;
+    if (cpb < TC_GROUP) cpb = TC_GROUP;
+    if (cpb > ncol) cpb = ncol;
+    TcTab *tab = nullptr;
+    if (e == cudaSuccess)
+        e = alloc_injected() ? cudaErrorMemoryAllocation
+                             : cudaMallocFromPoolAsync((void **)&tab, (size_t)cpb * per_col, pool, s);
+    ta.tab = tab;
+    for (int c0 = 0; c0 < ncol && e == cudaSuccess; c0 += (int)cpb) {
+        const int c1 = (int)std::min<long long>(ncol, c0 + cpb);
+        tc_tables_kernel<<<152 * 4, 256, 0, s>>>(l_max, mb_max, c0, c1, T, tab);
         e = cudaGetLastError();
+        ta.c0 = c0;
+        ta.c1 = c1;
+        const long long items = (long long)((c1 - c0 + TC_GROUP - 1) / TC_GROUP) * ta.n_chunks * ta.k_groups;
+        if (items > 0x7fffffffLL) e = cudaErrorInvalidValue;
+        for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+            ta.part = part;
+            conv_multi_tc_kernel<<<(unsigned)items, TC_THREADS, smem, s>>>(ta, T, amap);
+            e = cudaGetLastError();
+        }
     }
+    if (tab) cudaFreeAsync(tab, s);
     cudaFreeAsync(ea, s);
     return (int)e;
 }
