@@ -625,7 +625,7 @@ def _cube_block(W, dev, stream, args, mean_ms):
 
 def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
     """Several weight columns through one recursion on the L=4096 workload: four
-    Monte-Carlo skies with one beam (one pass, four outputs), 32 skies on the tensor cores
+    Monte-Carlo skies with one beam (one pass, four outputs), 64 skies on the tensor cores
     and the polarised total of three (sky, beam) pairs (one output).  Times per launch, column-evaluations per second,
     the speed-up over one wigner_conv_sum per column, and FP64 throughput counted as the
     headline's 5 flops per element plus 4 per summed element and column."""
@@ -651,10 +651,10 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
     ms_mc_s = timed(lambda: W.wigner_conv_sum_multi(beta, a4, b, form="fp64s", out=out4), 2)
     W.check_device_status()
     del out4, a4
-    # many skies on the tensor cores: 32 Monte-Carlo skies in one launch (split-bf16 slices,
-    # tcgen05.mma), against the same skies in 4-column passes of the split-pipe form (the
-    # passes are alike, so one pass is timed and counted 8 times)
-    K_TC = 32
+    # many skies on the tensor cores: 64 Monte-Carlo skies in one launch (split-bf16 slices,
+    # tcgen05.mma), against the same skies in ceil(64/4) = 16 passes of the 4-column
+    # split-pipe form (the passes are alike, so one pass is timed and counted 16 times)
+    K_TC = args.tc_skies
     a32 = torch.from_numpy(I.mc_skies(L_MAX, MS_MAX, K_TC, 200)).to(dev)
     out32 = torch.empty((K_TC, MB_MAX + 1, MS_MAX + 1, nb), dtype=torch.complex128, device=dev)
     ms_tc = timed(lambda: W.wigner_conv_sum_multi_tc(beta, a32, b, out=out32), 2)
@@ -670,7 +670,7 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
     for mb in range(MB_MAX + 1):
         for ms in range(MS_MAX + 1):
             tiles += (L_MAX + 1 - max(mb, ms) + 31) // 32
-    tiles *= (nb + 127) // 128
+    tiles *= ((nb + 127) // 128) * ((K_TC + 31) // 32)
     mma_tflops = tiles * 42 * 2.0 * 128 * 64 * 16 / (ms_tc / 1e3) / 1e12
     bf16_peak = _bf16_peak()
     ap, bp = I.polarised_columns(L_MAX, MB_MAX, MS_MAX, 100)
@@ -681,21 +681,21 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
     del outp
     torch.cuda.empty_cache()
     fl4 = 5 * n_elem + 4 * 4 * n_sum
-    return {"workload": f"{WORKLOAD}: 4 Monte-Carlo skies with one beam; polarised total of 3 pairs",
+    return {"workload": f"{WORKLOAD}: 4 Monte-Carlo skies with one beam; {args.tc_skies} skies on the tensor cores; polarised total of 3 pairs",
             "monte_carlo_4": {"ms_per_launch": ms_mc, "column_evals_per_s": 4 * n_elem / (ms_mc / 1e3),
                               "vs_separate_calls": 4 * mean_ms / ms_mc,
                               "fp64_tflops": fl4 / (ms_mc / 1e3) / 1e12},
             "monte_carlo_4_fp64s": {"ms_per_launch": ms_mc_s, "column_evals_per_s": 4 * n_elem / (ms_mc_s / 1e3),
                                     "vs_separate_fp64_calls": 4 * mean_ms / ms_mc_s},
             "polarised_total_3": {"ms_per_launch": ms_pol, "vs_separate_calls": 3 * mean_ms / ms_pol},
-            "monte_carlo_tc_32": {"ms_per_launch": ms_tc, "column_evals_per_s": K_TC * n_elem / (ms_tc / 1e3),
-                                  "vs_4col_fp64s_passes": (K_TC / 4) * ms_mc_s / ms_tc,
+            f"monte_carlo_tc_{K_TC}": {"skies": K_TC, "ms_per_launch": ms_tc, "column_evals_per_s": K_TC * n_elem / (ms_tc / 1e3),
+                                  "vs_4col_fp64s_passes": math.ceil(K_TC / 4) * ms_mc_s / ms_tc,
                                   "max_abs_diff_vs_4col_fp64s": tc_diff,
                                   "tensor": {"mma_tflops_executed": mma_tflops, "bf16_peak_tflops": bf16_peak,
                                              "frac": mma_tflops / bf16_peak,
                                              "note": "bf16 slice products issued by tcgen05.mma (42 per 32-order "
-                                                     "tile) over the measured cuBLAS bf16 peak; the launch is "
-                                                     "bound by the FP64 recursion, not the tensor pipe"},
+                                                     "tile and 32 skies) over the measured cuBLAS bf16 peak; the "
+                                                     "launch is bound by the FP64 recursion, not the tensor pipe"},
                                   "fp64_recursion_tflops": 5 * n_elem / (ms_tc / 1e3) / 1e12}}
 
 
@@ -981,6 +981,8 @@ def main(argv=None):
     p.add_argument("--skip-lmin", action="store_true", help="skip the l_min-cut timing")
     p.add_argument("--skip-multi", action="store_true", help="skip the several-column timing")
     p.add_argument("--skip-cube", action="store_true", help="skip the full-sum and data-cube timing")
+    p.add_argument("--tc-skies", type=int, default=64,
+                   help="Monte-Carlo skies of the tensor-core many-sky timing (default 64; fewer only for profiling)")
     p.add_argument("--dtable-steps", type=int, default=20)
     p.add_argument("--fp64s-steps", type=int, default=5)
     p.add_argument("--fp32x-steps", type=int, default=3)

@@ -29,23 +29,46 @@
 
 namespace wg {
 
-constexpr int LB = 16;  // l-block of the warp reduce-scatter
+constexpr int LB = 8;  // l-block of the warp reduce-scatter
 
-// v -> lane t holds the warp sum of v[t & 15] (float-float; LB values per lane)
-__device__ __forceinline__ void warp_reduce_scatter16_ff(ff (&v)[LB], int lane) {
+// (x.hi, x.lo) + (y.hi, y.lo) in float-float for a (re, im) pair with the packed f32x2
+// instructions: per lane the steps of ff_add (TwoSum, then Fast2Sum), a - b written
+// fma(b, -1, a) (one rounding, as a subtraction)
+__device__ __forceinline__ void ff_add2(float2 &xh, float2 &xl, float2 yh, float2 yl) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(xh, yh);
+    const float2 bb = __ffma2_rn(xh, m1, s);                         // s - xh
+    const float2 t1 = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, xh);     // xh - (s - bb)
+    const float2 e = __fadd2_rn(t1, __ffma2_rn(bb, m1, yh));         // + (yh - bb)
+    const float2 e2 = __fadd2_rn(e, __fadd2_rn(xl, yl));
+    const float2 h = __fadd2_rn(s, e2);
+    xl = __ffma2_rn(__ffma2_rn(s, m1, h), m1, e2);                   // e2 - (h - s)
+    xh = h;
+}
+
+// (vh, vl)[i], i < LB: the (re, im) float-float values of LB orders in every lane ->
+// lane t (t < LB) holds the warp sum of order t in (vh, vl)[0]
+__device__ __forceinline__ void warp_reduce_scatter_ff2(float2 (&vh)[LB], float2 (&vl)[LB], int lane) {
 #pragma unroll
-    for (int off = 8; off >= 1; off >>= 1) {
+    for (int off = LB / 2; off >= 1; off >>= 1) {
         const bool up = (lane & off) != 0;
 #pragma unroll
         for (int i = 0; i < off; ++i) {
-            const ff send = up ? v[i] : v[i + off];
-            const ff keep = up ? v[i + off] : v[i];
-            const ff got{__shfl_xor_sync(0xffffffffu, send.hi, off), __shfl_xor_sync(0xffffffffu, send.lo, off)};
-            v[i] = ff_add(keep, got);
+            const float2 sh = up ? vh[i] : vh[i + off], sl = up ? vl[i] : vl[i + off];
+            const float2 kh = up ? vh[i + off] : vh[i], kl = up ? vl[i + off] : vl[i];
+            const float2 gh = make_float2(__shfl_xor_sync(0xffffffffu, sh.x, off), __shfl_xor_sync(0xffffffffu, sh.y, off));
+            const float2 gl = make_float2(__shfl_xor_sync(0xffffffffu, sl.x, off), __shfl_xor_sync(0xffffffffu, sl.y, off));
+            vh[i] = kh;
+            vl[i] = kl;
+            ff_add2(vh[i], vl[i], gh, gl);
         }
     }
-    const ff got{__shfl_xor_sync(0xffffffffu, v[0].hi, 16), __shfl_xor_sync(0xffffffffu, v[0].lo, 16)};
-    v[0] = ff_add(v[0], got);
+#pragma unroll
+    for (int off = LB; off < 32; off <<= 1) {
+        const float2 gh = make_float2(__shfl_xor_sync(0xffffffffu, vh[0].x, off), __shfl_xor_sync(0xffffffffu, vh[0].y, off));
+        const float2 gl = make_float2(__shfl_xor_sync(0xffffffffu, vl[0].x, off), __shfl_xor_sync(0xffffffffu, vl[0].y, off));
+        ff_add2(vh[0], vl[0], gh, gl);
+    }
 }
 
 // Adjoint kernel with the forward kernels' normalised two-FMA recursion
@@ -57,7 +80,7 @@ template <int TL>
 struct SmemBwd {
     double2 sA[TL];       // (F0', G')  (phase 1: (F0, G))
     double2 sWd[TL];      // E weights (phase 1: w sqrt(...)), then times sigma_l
-    float4 sWE[TL];       // E weights as float-float
+    float4 sWE[TL];       // E weights as float-float: (re hi, im hi, re lo, im lo)
     long long sThr[TL];   // bit pattern of 1e-30 / sigma_l
     double sF2[TL];
     double sSig[TL + 1];
@@ -102,7 +125,7 @@ __global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, i
         const bool do_e = want_e && ms >= 1;
 
         double u[CPT], up[CPT];
-        ff gr[CPT], gi[CPT], er[CPT], ei[CPT];
+        float2 gh[CPT], gl[CPT], eh[CPT], el[CPT];  // G and E as float-float (re, im) pairs
         int nsc[CPT];
         bool plain[CPT];
 #pragma unroll
@@ -112,12 +135,11 @@ __global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, i
             nsc[c] = s.n;
             plain[c] = s.plain;
             up[c] = 0.0;
-            er[c] = ei[c] = ff{0.f, 0.f};
-            gr[c] = gi[c] = ff{0.f, 0.f};
+            eh[c] = el[c] = gh[c] = gl[c] = make_float2(0.f, 0.f);
             if (do_s && valid[c]) {
                 const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[((size_t)mb * MS1 + ms) * NB + jj[c]];
-                gr[c] = ff{__double2float_rn(g.x), __double2float_rn(g.x - (double)__double2float_rn(g.x))};
-                gi[c] = ff{__double2float_rn(g.y), __double2float_rn(g.y - (double)__double2float_rn(g.y))};
+                dbl_to_ff(g.x, gh[c].x, gl[c].x);
+                dbl_to_ff(g.y, gh[c].y, gl[c].y);
             }
         }
         double sig_m1 = 0.0, sig_0 = 1.0;
@@ -168,8 +190,8 @@ __global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, i
                 sm.sA[i] = fg;
                 const double2 w = sm.sWd[i];
                 float4 wf;
-                dbl_to_ff(w.x * sg, wf.x, wf.y);
-                dbl_to_ff(w.y * sg, wf.z, wf.w);
+                dbl_to_ff(w.x * sg, wf.x, wf.z);
+                dbl_to_ff(w.y * sg, wf.y, wf.w);
                 sm.sWE[i] = wf;
                 sm.sThr[i] = __double_as_longlong(WG_EPS_SUM / sg);
             }
@@ -178,11 +200,11 @@ __global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, i
             for (int blk = 0; blk < TL / LB; ++blk) {
                 const int lb = ts + blk * LB;
                 if (lb > L) break;  // uniform over the CTA
-                ff sr[LB], si[LB];
+                float2 sh[LB], sl[LB];  // S of the block's orders: (re, im) float-float
 #pragma unroll
                 for (int i = 0; i < LB; ++i) {
                     const int l = lb + i;
-                    sr[i] = si[i] = ff{0.f, 0.f};
+                    sh[i] = sl[i] = make_float2(0.f, 0.f);
                     if (l <= L) {  // uniform
                         const int ti = blk * LB + i;
                         const float4 we = sm.sWE[ti];
@@ -193,14 +215,9 @@ __global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, i
                             // this also keeps split_ff inside its range (|u| >= 2^-100)
                             ff uu = split_ff(u[c]);
                             if (!plain[c] || !abs_ge(u[c], thr)) uu = ff{0.f, 0.f};
-                            if (do_s) {
-                                ff_mac(sr[i], gr[c].hi, gr[c].lo, uu.hi, uu.lo);
-                                ff_mac(si[i], gi[c].hi, gi[c].lo, uu.hi, uu.lo);
-                            }
-                            if (do_e) {
-                                ff_mac(er[c], we.x, we.y, uu.hi, uu.lo);
-                                ff_mac(ei[c], we.z, we.w, uu.hi, uu.lo);
-                            }
+                            if (do_s) ff_mac2(sh[i], sl[i], gh[c], gl[c], uu.hi, uu.lo);
+                            if (do_e)
+                                ff_mac2(eh[c], el[c], make_float2(we.x, we.y), make_float2(we.z, we.w), uu.hi, uu.lo);
                         }
                         if (l < L) {
                             const double2 fg = sm.sA[ti];
@@ -216,9 +233,8 @@ __global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, i
                     }
                 }
                 if (do_s) {
-                    warp_reduce_scatter16_ff(sr, lane);
-                    warp_reduce_scatter16_ff(si, lane);
-                    if (lane < LB) sm.sRed[blk][warp][lane] = make_float4(sr[0].hi, sr[0].lo, si[0].hi, si[0].lo);
+                    warp_reduce_scatter_ff2(sh, sl, lane);
+                    if (lane < LB) sm.sRed[blk][warp][lane] = make_float4(sh[0].x, sl[0].x, sh[0].y, sl[0].y);
                 }
             }
             __syncthreads();
@@ -255,8 +271,8 @@ __global__ void __launch_bounds__(NT) conv_bwd_kernel(ConvBwdArgs A, Tables T, i
                 const double2 g = reinterpret_cast<const double2 *>(A.grad_c)[o];
                 const double2 cf = reinterpret_cast<const double2 *>(A.c_fwd)[o];
                 const double coef = ((double)(ms - 1) * ang[c].cb - (double)mb) / ang[c].sb;
-                const double vr = coef * cf.x - ((double)er[c].hi + (double)er[c].lo);
-                const double vi = coef * cf.y - ((double)ei[c].hi + (double)ei[c].lo);
+                const double vr = coef * cf.x - ((double)eh[c].x + (double)el[c].x);
+                const double vi = coef * cf.y - ((double)eh[c].y + (double)el[c].y);
                 partial[o] = g.x * vr + g.y * vi;
             }
         }
@@ -330,7 +346,7 @@ __global__ void __launch_bounds__(NT) grad_b_kernel(const double *S, const doubl
 }
 
 int launch_conv_bwd(const ConvBwdArgs &a, const Tables &t, void *stream_) {
-    constexpr int NT = 128, CPT = 2, TL = 64;
+    constexpr int NT = 256, CPT = 2, TL = 128;
     cudaStream_t stream = (cudaStream_t)stream_;
     const int MB1 = a.mb_max + 1, MS1 = a.ms_max + 1;
     const bool want_s = a.grad_a || a.grad_b;

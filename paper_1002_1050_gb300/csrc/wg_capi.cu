@@ -57,17 +57,21 @@ std::atomic<int> g_wait_tries{WG_WAIT_TRIES_DEFAULT};
 // Host-side construction of the constant tables (Sec. 4.2.2 and Sec. 3.2):
 //   ln n! for n <= 2 lcap + 1 as a double-double from long double lgamma,
 //   P_i = sqrt(1/(i+1)), Q_i = sqrt(i/(i+1)) for i <= 2 lcap + 1,
-//   R1_l = 1/(l(l+1)), R2_l = (l+1)/l for 1 <= l <= lcap (0 at l = 0).
+//   R1_l = 1/(l(l+1)), R2_l = (l+1)/l for 1 <= l <= lcap (0 at l = 0);
+// and, for the FP32 form only, E(n) = ln((n-1)!! / n!!) for n <= 2 lcap + 1 as float-float:
+//   E(2p) = ln (2p)! - 2 ln p! - 2p ln 2,  E(2p+1) = 2 ln p! + 2p ln 2 - ln (2p+1)!
+// ((2p)!! = 2^p p!, (2p+1)!! = (2p+1)! / (2^p p!)).
 void build_tables(int lcap, std::vector<double> &h) {
     const size_t n2 = 2 * (size_t)lcap + 2;
     const size_t n1 = (size_t)lcap + 1;
     // doubles: lnf_hi, lnf_lo, P, Q (n2 each), R1, R2 (n1 each); then float2 copies of
-    // ln n!, P, Q (n2 each), R1, R2 (n1 each), one float2 per double slot
-    h.assign(4 * n2 + 2 * n1 + 3 * n2 + 2 * n1, 0.0);
+    // ln n!, P, Q (n2 each), R1, R2 (n1 each), then E (n2), one float2 per double slot
+    h.assign(4 * n2 + 2 * n1 + 3 * n2 + 2 * n1 + n2, 0.0);
     double *lnf_hi = h.data(), *lnf_lo = lnf_hi + n2, *P = lnf_lo + n2, *Q = P + n2;
     double *R1 = Q + n2, *R2 = R1 + n1;
     float *F = reinterpret_cast<float *>(R2 + n1);
     float *lnf_f = F, *P_f = lnf_f + 2 * n2, *Q_f = P_f + 2 * n2, *R1_f = Q_f + 2 * n2, *R2_f = R1_f + 2 * n1;
+    float *E_f = R2_f + 2 * n1;
     auto put_ff = [](float *dst, long double v) {
         const float hi = (float)v;
         dst[0] = hi;
@@ -93,6 +97,13 @@ void build_tables(int lcap, std::vector<double> &h) {
         R2[l] = (double)r2;
         put_ff(R1_f + 2 * l, r1);
         put_ff(R2_f + 2 * l, r2);
+    }
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    for (size_t n = 0; n < n2; ++n) {
+        const long double p = (long double)(n / 2);
+        const long double lfp = lgammal(p + 1.0L), lfn = lgammal((long double)n + 1.0L);
+        const long double e = (n & 1) ? 2.0L * lfp + 2.0L * p * ln2 - lfn : lfn - 2.0L * lfp - 2.0L * p * ln2;
+        put_ff(E_f + 2 * n, e);
     }
 }
 
@@ -165,6 +176,7 @@ int get_tables(int l_max, wg::Tables *t, DevState **out_state = nullptr) {
     t->Q_f = F + 2 * n2;
     t->R1_f = F + 3 * n2;
     t->R2_f = F + 3 * n2 + n1;
+    t->E_f = F + 3 * n2 + 2 * n1;
     t->lcap = s.lcap;
     t->status = s.status;
     (void)n1;
@@ -223,6 +235,8 @@ int check_ptr(const void *p, size_t align, const char *name) {
     } while (0)
 
 int launch_rc(int err, const char *what) {
+    if (err == (int)cudaErrorMemoryAllocation)  // a launcher's stream-ordered scratch
+        return fail(WG_ERR_ALLOC, std::string(what) + ": " + cudaGetErrorString(cudaErrorMemoryAllocation));
     if (err != 0) return cuda_fail((cudaError_t)err, what);
     return WG_OK;
 }

@@ -129,6 +129,24 @@ __device__ __forceinline__ float d2f_trunc(double x) {
                            (unsigned)(((unsigned long long)b & 0xfffffffffffffULL) >> 29));
 }
 
+// x 2^-shift as a float, rounded to nearest (ties to even), on the integer pipe: the
+// exponent is re-biased in the double's bit pattern and the 29 dropped mantissa bits
+// rounded (a carry out of the mantissa moves into the exponent, as it should).  Zero and
+// subnormal doubles give a signed zero, results below 2^-126 flush to a signed zero, and
+// results from 2^128 up (or an infinite or NaN x) are infinite or NaN.
+__device__ __forceinline__ float d2f_rn_scaled(double x, int shift) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int ef = (int)((b >> 52) & 0x7ff);
+    if (ef == 0x7ff) return __uint_as_float(sign | ((b & 0xfffffffffffffULL) ? 0x7fc00000u : 0x7f800000u));
+    const int e = ef - 1023 - shift;  // unbiased exponent of the result
+    if (ef == 0 || e < -126) return __uint_as_float(sign);
+    if (e > 127) return __uint_as_float(sign | 0x7f800000u);
+    unsigned long long r = ((unsigned long long)(e + 127) << 52) | (b & 0xfffffffffffffULL);
+    r += 0x0fffffffULL + ((r >> 29) & 1);
+    return __uint_as_float(sign | (unsigned)(r >> 29));
+}
+
 // acc += w * u in float-float (Dekker product with FMA, Knuth TwoSum, Fast2Sum)
 __device__ __forceinline__ void ff_mac(ff &acc, float wh, float wl, float uh, float ul) {
     const float p = __fmul_rn(wh, uh);
@@ -234,12 +252,13 @@ struct Tables {
     const double *R1;      // 1/(l(l+1)), l >= 1  (R1[0] = 0)
     const double *R2;      // (l+1)/l,    l >= 1  (R2[0] = 0)
     // float-float copies (hi, lo) for the FP32 form's set-up on the FP32 pipe; may be
-    // null for paths that do not use them: ln n!, P_i, Q_i (2*lcap+2 each), R1, R2 (lcap+1)
+    // null for paths that do not use them: ln n!, P_i, Q_i, E (2*lcap+2 each), R1, R2 (lcap+1)
     const float2 *lnf_f;
     const float2 *P_f;
     const float2 *Q_f;
     const float2 *R1_f;
     const float2 *R2_f;
+    const float2 *E_f;     // E(n) = ln((n-1)!! / n!!), n <= 2*lcap+1 (FP32 form's sigma)
     int lcap;
     int *status;           // device status word (WG_DEVERR_* bits)
 };
@@ -259,28 +278,54 @@ struct Scaled {
     bool plain;
 };
 
-// ln|d^{l0}| of the seed in double-double, its sign, and whether the value is exactly 0.
-__device__ __forceinline__ dd seed_log(int mb, int ms, const Angle &t, const Tables &T, double &sign, bool &zero) {
+// The angle-independent part of ln|d^{l0}|, (ln (2l0)! - ln (l0+m)! - ln (l0-m)!)/2, in
+// double-double: one value per chain column, shared by all its angles.
+__device__ __forceinline__ dd seed_prefactor(int mb, int ms, const Tables &T) {
     const int l0 = mb > ms ? mb : ms;
     const int m = mb > ms ? ms : mb;
     const int p = l0 + m, q = l0 - m;
-    zero = (p > 0 && t.c_zero) || (q > 0 && t.s_zero);  // a factor is exactly 0 (Sec. 3.2 early stop)
-    sign = (mb > ms && (q & 1)) ? -1.0 : 1.0;
     dd x = {T.lnf_hi[2 * l0], T.lnf_lo[2 * l0]};
     x = dd_add(x, dd_neg(dd{T.lnf_hi[p], T.lnf_lo[p]}));
     x = dd_add(x, dd_neg(dd{T.lnf_hi[q], T.lnf_lo[q]}));
     x.hi *= 0.5;  // exact
     x.lo *= 0.5;
+    return x;
+}
+
+// ln|d^{l0}| of the seed in double-double from the column's prefactor, its sign, and
+// whether the value is exactly 0.
+__device__ __forceinline__ dd seed_log_from(dd x, int mb, int ms, const Angle &t, double &sign, bool &zero) {
+    const int l0 = mb > ms ? mb : ms;
+    const int m = mb > ms ? ms : mb;
+    const int p = l0 + m, q = l0 - m;
+    zero = (p > 0 && t.c_zero) || (q > 0 && t.s_zero);  // a factor is exactly 0 (Sec. 3.2 early stop)
+    sign = (mb > ms && (q & 1)) ? -1.0 : 1.0;
     if (p > 0 && !zero) x = dd_add(x, dd_mul_d(dd{t.lnc, 0.0}, (double)p));
     if (q > 0 && !zero) x = dd_add(x, dd_mul_d(dd{t.lns, 0.0}, (double)q));
     return x;
 }
 
-__device__ __forceinline__ Scaled seed_value(int mb, int ms, const Angle &t, const Tables &T) {
-    Scaled r;
+// ln|d^{l0}| of the seed in double-double, its sign, and whether the value is exactly 0.
+__device__ __forceinline__ dd seed_log(int mb, int ms, const Angle &t, const Tables &T, double &sign, bool &zero) {
+    return seed_log_from(seed_prefactor(mb, ms, T), mb, ms, t, sign, zero);
+}
+
+// The seed as a scaled double from ln|d^{l0}| (x), its sign and zero flag.
+__device__ __forceinline__ Scaled seed_from_log(dd x, double sign, bool zero);
+
+__device__ __forceinline__ Scaled seed_value_from(dd pre, int mb, int ms, const Angle &t) {
     double sign;
     bool zero;
-    dd x = seed_log(mb, ms, t, T, sign, zero);
+    const dd x = seed_log_from(pre, mb, ms, t, sign, zero);
+    return seed_from_log(x, sign, zero);
+}
+
+__device__ __forceinline__ Scaled seed_value(int mb, int ms, const Angle &t, const Tables &T) {
+    return seed_value_from(seed_prefactor(mb, ms, T), mb, ms, t);
+}
+
+__device__ __forceinline__ Scaled seed_from_log(dd x, double sign, bool zero) {
+    Scaled r;
     if (zero) {
         r.mant = 0.0;
         r.n = 0;

@@ -2,6 +2,7 @@
 // device code and the precision design are described in wg_fp32x.cuh.
 #include <cuda_runtime.h>
 
+#include "../../include/wigner.h"
 #include "wg_fp32x.cuh"
 
 namespace wg {
@@ -21,21 +22,61 @@ __global__ void __launch_bounds__(NT, 6) conv_fp32x_kernel(ConvArgs A, Tables T,
     flush_counters(A.counters, n_elem, n_sum);
 }
 
+// Per-column power-of-two scales of the FP32 form's weights: ea[ms] = e with max over l
+// of |a[l][ms]| (re and im) in [2^(e-1), 2^e), eb[mb] likewise for b (0 for a zero
+// column), so that the scaled weights stay in float's range whatever the columns'
+// magnitudes.  Threads 0..ms_max take a's columns, the next mb_max + 1 threads b's.
+__global__ void fp32x_scales_kernel(const double *a, const double *b, int L, int MB, int MS, int *ea, int *eb) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool is_a = t <= MS;
+    const int c = is_a ? t : t - (MS + 1);
+    if (!is_a && c > MB) return;
+    const int stride = is_a ? MS + 1 : MB + 1;
+    const double2 *col = reinterpret_cast<const double2 *>(is_a ? a : b) + c;
+    int m = 0;
+    for (int l = 0; l <= L; ++l) {
+        const double2 v = col[(size_t)l * stride];
+        m = max(m, max(biased_exp(v.x), biased_exp(v.y)));
+    }
+    (is_a ? ea : eb)[c] = m == 0 ? 0 : m - 1022;
+}
+
+int host_pool(cudaMemPool_t *pool);  // wg_host.cu
+
 template <int NT, int CPT, int TL>
-static int launch_conv_fp32x_t(const ConvArgs &a, const Tables &t, void *stream, int group) {
+static int launch_conv_fp32x_t(const ConvArgs &a_in, const Tables &t, void *stream, int group) {
     const int per_chunk = NT * CPT;
-    const int n_chunks = (a.n_beta + per_chunk - 1) / per_chunk;
-    const int ncol = (a.mb_max + 1) * (a.ms_max + 1);
-    const int nk = (a.k_hi < 0 ? ncol : a.k_hi) - a.k_lo;
+    const int n_chunks = (a_in.n_beta + per_chunk - 1) / per_chunk;
+    const int ncol = (a_in.mb_max + 1) * (a_in.ms_max + 1);
+    const int nk = (a_in.k_hi < 0 ? ncol : a_in.k_hi) - a_in.k_lo;
     const long long items = (long long)n_chunks * ((nk + group - 1) / group);
     if (items == 0) return 0;
     if (items > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-    conv_fp32x_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, (cudaStream_t)stream>>>(a, t, n_chunks, group);
-    return (int)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    // the weight scales, in stream-ordered scratch from the library's pool
+    cudaMemPool_t pool;
+    if (host_pool(&pool) != WG_OK) return (int)cudaErrorMemoryAllocation;
+    ConvArgs a = a_in;
+    int *sc = nullptr;
+    const int n_sc = a.ms_max + 1 + a.mb_max + 1;
+    cudaError_t e = alloc_injected() ? cudaErrorMemoryAllocation
+                                     : cudaMallocFromPoolAsync((void **)&sc, (size_t)n_sc * sizeof(int), pool, s);
+    if (e != cudaSuccess) return (int)e;
+    a.ea = sc;
+    a.eb = sc + a.ms_max + 1;
+    fp32x_scales_kernel<<<(unsigned)((n_sc + 127) / 128), 128, 0, s>>>(a.a, a.b, a.l_max, a.mb_max, a.ms_max,
+                                                                       const_cast<int *>(a.ea), const_cast<int *>(a.eb));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        conv_fp32x_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, s>>>(a, t, n_chunks, group);
+        e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(sc, s);
+    return (int)(e != cudaSuccess ? e : ef);
 }
 
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream) {
-    return launch_conv_fp32x_t<128, 4, 128>(a, t, stream, 16);
+    return launch_conv_fp32x_t<128, 4, 120>(a, t, stream, 16);
 }
 
 // ---------------------------------------------------------------------------

@@ -152,17 +152,23 @@ __device__ __forceinline__ void fixup32(float &cur, float &aux, int &n) {
 // float-float on the FP32 pipe from the float-float tables and rounded to float:
 // K0 = F0 (1 - F1) - 1 - F2 and K1 = F0 (1 + F1) - 1 - F2 are small where the form
 // matters and keep their relative precision because the cancellation happens in ff.
+// F0 and G = F0 F1 of Eq. lrec at order l < l_max in float-float (Sec. 4.2.2's tables)
+__device__ __forceinline__ void f0g_ff(int l, int mb, int ms, const Tables &T, ff &f0, ff &g) {
+    const ff pp = ff_mul(ff_mul(ff_of(T.P_f[l + mb]), ff_of(T.P_f[l - mb])),
+                         ff_mul(ff_of(T.P_f[l + ms]), ff_of(T.P_f[l - ms])));
+    f0 = ff_mul(ff_int((long long)(l + 1) * (2 * l + 1)), pp);
+    g = ff_mul(f0, ff_mul(ff_int((long long)mb * ms), ff_of(T.R1_f[l])));
+}
+
 __device__ __forceinline__ float4 diff_coefficients(int l, int L, int mb, int ms, const Tables &T, float4 &raw) {
     if (l >= L) {
         raw = make_float4(0.f, 0.f, 1.f, 0.f);
         return make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const ff pp = ff_mul(ff_mul(ff_of(T.P_f[l + mb]), ff_of(T.P_f[l - mb])),
-                         ff_mul(ff_of(T.P_f[l + ms]), ff_of(T.P_f[l - ms])));
     const ff qq = ff_mul(ff_mul(ff_of(T.Q_f[l + mb]), ff_of(T.Q_f[l - mb])),
                          ff_mul(ff_of(T.Q_f[l + ms]), ff_of(T.Q_f[l - ms])));
-    const ff f0 = ff_mul(ff_int((long long)(l + 1) * (2 * l + 1)), pp);
-    const ff g = ff_mul(f0, ff_mul(ff_int((long long)mb * ms), ff_of(T.R1_f[l])));
+    ff f0, g;
+    f0g_ff(l, mb, ms, T, f0, g);
     const ff f2 = ff_mul(ff_of(T.R2_f[l]), qq);
     const ff base = ff_add(ff_add(f0, ff{-1.0f, 0.0f}), ff_neg(f2));
     const ff k0 = ff_add(base, ff_neg(g));
@@ -206,6 +212,29 @@ __device__ __forceinline__ void step_pairs(const float4 a4, const float2 (&kp)[N
     }
 }
 
+// The difference-form step without its term, for warps whose chains are all below
+// 2^-128 (sp = 0: their terms are zero)
+template <int NP>
+__device__ __forceinline__ void step_pairs_rec(const float4 a4, const float2 (&kp)[NP], const float2 (&x2p)[NP],
+                                               float2 (&cur)[NP], float2 (&aux)[NP]) {
+    const float2 A = make_float2(a4.x, a4.y), F2 = make_float2(a4.z, a4.w);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float2 coef = __ffma2_rn(A, x2p[p], kp[p]);
+        aux[p] = __ffma2_rn(F2, aux[p], __fmul2_rn(coef, cur[p]));
+        cur[p] = __fadd2_rn(cur[p], aux[p]);
+    }
+}
+
+// whether some chain of the warp has a non-zero term factor sp (warp-uniform)
+template <int NP>
+__device__ __forceinline__ bool warp_terms_live(const float2 (&sp)[NP]) {
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) any = any || sp[p].x != 0.0f || sp[p].y != 0.0f;
+    return __any_sync(0xffffffffu, any);
+}
+
 // Rescaling of one scaled chain, run every RESCALE_EVERY steps of a masked tile: a
 // mantissa at or above 2^64 is scaled by 2^-64 (n += 1), one of a scaled chain below
 // 2^-64 by 2^64 (n -= 1), jointly with aux; then sp = 2^(64 n) (0 for n <= -2).  No
@@ -235,12 +264,27 @@ __device__ __forceinline__ void rescale_pairs(float2 (&cur)[NP], float2 (&aux)[N
     }
 }
 
-// One l-step of the NP chain pairs in the normalised form (bulk angles): the chain is
-// carried as u^l = d^l / sigma_l (sigma_{l0} = sigma_{l0+1} = 1, sigma_{l+1} =
-// F2_l sigma_{l-1}), so Eq. lrec reads u^{l+1} = (F0'_l cos b - G'_l) u^l - u^{l-1}
-// with F0' = F0 rho_l, G' = G rho_l, rho_l = sigma_l / sigma_{l+1}: two packed
-// instructions per pair for the recursion, two for the sum of (w_l sigma_l) u^l.
-// n4 = (F0', F0', -G', -G'), w4 = (w sigma)(re, re, im, im).
+// the normalised step without its term (a warp whose chains are all below 2^-128)
+template <int NP>
+__device__ __forceinline__ void step_norm_rec(const float4 n4, const float2 (&cbp)[NP], float2 (&u)[NP],
+                                              float2 (&up)[NP]) {
+    const float2 F = make_float2(n4.x, n4.y), NG = make_float2(n4.z, n4.w);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float2 y = __ffma2_rn(F, cbp[p], NG);
+        const float2 nx = __ffma2_rn(y, u[p], up[p]);
+        up[p] = u[p];
+        u[p] = nx;
+    }
+}
+
+// One l-step of the NP chain pairs in the normalised form (bulk angles): with u^l =
+// d^l / sigma_l (sigma_{l0} = sigma_{l0+1} = 1, sigma_{l+1} = F2_l sigma_{l-1}), Eq. lrec
+// reads u^{l+1} = (F0'_l cos b - G'_l) u^l - u^{l-1}, F0' = F0 rho_l, G' = G rho_l,
+// rho_l = sigma_l / sigma_{l+1}; the chain is carried as v^l = s_k u^l, s_k = +1, +1,
+// -1, -1, ... for k = l - l0, which obeys v^{l+1} = (-1)^k (F0'_l cos b - G'_l) v^l +
+// v^{l-1}: two packed FMAs per pair for the recursion, two for the sum of (w_l sigma_l
+// s_k) v^l.  n4 = (-1)^k (F0', F0', -G', -G'), w4 = (w sigma s)(re, re, im, im).
 template <int NP, int PAR, bool MASKED>
 __device__ __forceinline__ void step_norm(const float4 n4, const float4 w4, const float2 (&cbp)[NP],
                                           float2 (&u)[NP], float2 (&up)[NP], const float2 (&sp)[NP],
@@ -253,117 +297,108 @@ __device__ __forceinline__ void step_norm(const float4 n4, const float4 w4, cons
         pr[PAR][p] = __ffma2_rn(WR, cm, pr[PAR][p]);
         pi[PAR][p] = __ffma2_rn(WI, cm, pi[PAR][p]);
         const float2 y = __ffma2_rn(F, cbp[p], NG);
-        const float2 nx = __ffma2_rn(y, u[p], make_float2(-up[p].x, -up[p].y));
+        const float2 nx = __ffma2_rn(y, u[p], up[p]);
         up[p] = u[p];
         u[p] = nx;
     }
 }
 
-// Shared memory of one FP32-form CTA: two buffers of the difference form's l-tile
-// operands (the tile after the current one is built while other warps still step the
-// current one), one of the normalised form's (built from the raw coefficients after a
-// barrier), and the per-chain state that is touched once per column or per tile (kept
-// out of registers so that more warps fit on an SM): the seeds' half-angle
-// logarithms and flags, and the Neumaier-compensated sums.
+// Shared memory of one FP32-form CTA: two buffers of each form's l-tile operands (the
+// tile after the current one is built while other warps still step the current one),
+// and the per-chain state that is touched once per column or per tile (kept out of
+// registers so that more warps fit on an SM): the seeds' half-angle logarithms and
+// flags, and the Neumaier-compensated sums.
 template <int NT, int CPT, int TL>
 struct SmemFp32 {
-    float4 sA[2][TL];       // (A, A, F2, F2), A = -2 F0
+    float4 sA[2][TL];       // difference form: (A, A, F2, F2), A = -2 F0
     float4 sK[2][TL];       // (K0, K0, K1, K1)
     float4 sW[2][TL];       // (w_re, w_re, w_im, w_im)
-    float4 sRaw[TL];        // (F0, G, F2 hi, F2 lo) of the tile being built
-    float4 sN[TL];          // (F0', F0', -G', -G') of the normalised form
-    float4 sWn[TL];         // (w sigma)(re, re, im, im)
-    float4 sSig;            // sigma at the entries -1 and 0 of the next tile (float-float)
+    float4 sN[2][TL];       // normalised form: (F0', F0', -G', -G')
+    float4 sWn[2][TL];      // (w sigma s)(re, re, im, im)
+    float4 sKc;             // the column's S(l0), S(l0 + 1) (float-float; see sigma_log)
     float4 sLog[CPT][NT];   // (ln cos(b/2) hi, lo, ln sin(b/2) hi, lo)
     int sFlag[CPT][NT];     // bit 0: bad angle, 1: mirrored, 2: cos(b/2) = 0, 3: sin(b/2) = 0
     float4 sAcc[CPT][NT];   // compensated sums (re, re carry, im, im carry)
 };
 
-// operands of order l (<= L) of column (mb, ms) into tile entry i of buffer buf; F2 of
-// the first order l0 is entered as 1 (sigma_{l0+1} = sigma_{l0}), as is F2 past l_max
-template <int NT, int CPT, int TL>
-__device__ __forceinline__ void build_tile_entry(const ConvArgs &A, const Tables &T, int l, int l0, int mb, int ms,
-                                                 SmemFp32<NT, CPT, TL> &sm, int buf, int i) {
-    const int MB1 = A.mb_max + 1;
-    const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
-    const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
-    const float ar = d2f_trunc(av.x), ai = d2f_trunc(av.y);
-    const float br = d2f_trunc(bv.x), bi = d2f_trunc(bv.y);
-    const float wr = __fmaf_rn(br, ar, bi * ai), wi = __fmaf_rn(br, ai, -(bi * ar));
-    float4 raw;
-    const float4 c = diff_coefficients(l, A.l_max, mb, ms, T, raw);
-    if (l == l0) {
-        raw.z = 1.0f;
-        raw.w = 0.0f;
-    }
-    sm.sA[buf][i] = make_float4(c.x, c.x, c.y, c.y);
-    sm.sK[buf][i] = make_float4(c.z, c.z, c.w, c.w);
-    sm.sW[buf][i] = make_float4(wr, wr, wi, wi);
-    sm.sRaw[i] = raw;
+// The normalisation sigma of the normalised form in closed form.  sigma_{l0} =
+// sigma_{l0+1} = 1 and sigma_{l+1} = F2_l sigma_{l-1}; with h_l = sqrt((l^2 - mb^2)(l^2 -
+// ms^2)) / l, Eq. lrec's F2_l = h_l / h_{l+1}, so along each parity of l the product
+// telescopes into alternating logarithms of h, and those of each factor l +- m of h
+// into logarithms of double factorials: ln sigma_l = S(l) - S(l0 + ((l - l0) & 1)) with
+//   S(n) = (E(n - mb) + E(n + mb) + E(n - ms) + E(n + ms)) / 2 - E(n),
+//   E(n) = ln((n-1)!! / n!!)   (a host table, float-float).
+// Each entry of a tile is then independent of the others (no scan along l).
+__device__ __forceinline__ ff sigma_log(int n, int mb, int ms, const float2 *E) {
+    ff s = ff_add(ff_add(ff_of(E[n - mb]), ff_of(E[n + mb])), ff_add(ff_of(E[n - ms]), ff_of(E[n + ms])));
+    s.hi *= 0.5f;
+    s.lo *= 0.5f;
+    return ff_add(s, ff_neg(ff_of(E[n])));
 }
 
-// The normalised form's operands of a built tile, by one warp: sigma over the tile by
-// a float-float product scan of F2 along each parity of l, sigma_{e+1} = F2_e
-// sigma_{e-1} (carry in sSig: sigma at the entries -1 and 0, replaced by the next
-// tile's), then rho = sigma_e / sigma_{e+1}, F0' = F0 rho, G' = G rho, w sigma.  Lane t
-// owns entries EPL t .. EPL t + EPL - 1.
+// e^x of a float-float argument, to float accuracy
+__device__ __forceinline__ float ff_expf(ff x) {
+    const float e = expf(x.hi);
+    return __fmaf_rn(e, x.lo, e);
+}
+
+// The operands of the l-tile starting at order ts into buffer buf, for the forms in use
+// (need_diff, need_norm: CTA-uniform).  Warp w builds entries 31 w + lane (lane < 31);
+// each lane also forms S(l) of its order for the normalised form, and takes S(l+1)
+// from the next lane (lane 31 forms the first order of the next warp's entries).
+// sm.sKc holds S(l0) and S(l0 + 1).  F0 = G = 0 from l_max on (the chain's last step is
+// never used).
 template <int NT, int CPT, int TL>
-__device__ __forceinline__ void normalise_tile(SmemFp32<NT, CPT, TL> &sm, int buf, int nl, int lane) {
-    constexpr int EPL = TL / 32;
-    static_assert(TL % 64 == 0, "an even number of entries per lane");
-    const int e0 = EPL * lane;
-    // products of the lane's factors on each parity chain
-    ff pe{1.0f, 0.0f}, po{1.0f, 0.0f};  // factors of odd entries (even chain), of even entries (odd chain)
-#pragma unroll
-    for (int q = 0; q < EPL; ++q) {
-        const float4 r = sm.sRaw[e0 + q];
-        const ff f = (e0 + q < nl) ? ff{r.z, r.w} : ff{1.0f, 0.0f};
-        if (q & 1)
-            pe = ff_mul(pe, f);
-        else
-            po = ff_mul(po, f);
-    }
-    // inclusive product scans over the lanes, then exclusive
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const ff e{__shfl_up_sync(0xffffffffu, pe.hi, off), __shfl_up_sync(0xffffffffu, pe.lo, off)};
-        const ff o{__shfl_up_sync(0xffffffffu, po.hi, off), __shfl_up_sync(0xffffffffu, po.lo, off)};
-        if (lane >= off) {
-            pe = ff_mul(pe, e);
-            po = ff_mul(po, o);
+__device__ __forceinline__ void build_tile(const ConvArgs &A, const Tables &T, int ts, int l0, int mb, int ms,
+                                           bool need_diff, bool need_norm, SmemFp32<NT, CPT, TL> &sm, int buf) {
+    constexpr int PER = 31 * (NT / 32);
+    const int L = A.l_max, MB1 = A.mb_max + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < TL; base += PER) {
+        const int i = base + 31 * w + lane;
+        const int l = ts + i;
+        ff s{0.0f, 0.0f};
+        if (need_norm && i <= TL && l <= L + 1) s = sigma_log(l, mb, ms, T.E_f);
+        const ff sn{__shfl_down_sync(0xffffffffu, s.hi, 1), __shfl_down_sync(0xffffffffu, s.lo, 1)};
+        if (lane == 31 || i >= TL || l > L) continue;
+        const double2 av = reinterpret_cast<const double2 *>(A.a)[(size_t)l * (A.ms_max + 1) + ms];
+        const double2 bv = reinterpret_cast<const double2 *>(A.b)[(size_t)l * MB1 + mb];
+        const int sa = A.ea ? A.ea[ms] : 0, sb = A.eb ? A.eb[mb] : 0;
+        const float ar = d2f_rn_scaled(av.x, sa), ai = d2f_rn_scaled(av.y, sa);
+        const float br = d2f_rn_scaled(bv.x, sb), bi = d2f_rn_scaled(bv.y, sb);
+        const float wr = __fmaf_rn(br, ar, bi * ai), wi = __fmaf_rn(br, ai, -(bi * ar));
+        float f0 = 0.0f, g = 0.0f;
+        if (need_diff) {
+            float4 raw;
+            const float4 c = diff_coefficients(l, L, mb, ms, T, raw);
+            sm.sA[buf][i] = make_float4(c.x, c.x, c.y, c.y);
+            sm.sK[buf][i] = make_float4(c.z, c.z, c.w, c.w);
+            sm.sW[buf][i] = make_float4(wr, wr, wi, wi);
+            f0 = raw.x;
+            g = raw.y;
+        } else if (l < L) {
+            ff f0f, gf;
+            f0g_ff(l, mb, ms, T, f0f, gf);
+            f0 = f0f.hi;
+            g = gf.hi;
+        }
+        if (need_norm) {
+            const float4 kc = sm.sKc;
+            const int k = l - l0;
+            const ff ke{(k & 1) ? kc.z : kc.x, (k & 1) ? kc.w : kc.y}, ko{(k & 1) ? kc.x : kc.z, (k & 1) ? kc.y : kc.w};
+            const ff ls = ff_add(s, ff_neg(ke));
+            const ff lsn = ff_add(sn, ff_neg(ko));
+            const float sig = ff_expf(ls);                      // sigma_l
+            const float rho = ff_expf(ff_add(ls, ff_neg(lsn)));  // sigma_l / sigma_{l+1}
+            // the chain is carried as v = s_k u with s_k = +1, +1, -1, -1, ... (k = l - l0):
+            // v^{l+1} = (-1)^k y_l v^l + v^{l-1}, so the step takes no negation, and
+            // d^l = sigma_l s_k v^l
+            const float f0p = ((k & 1) ? -f0 : f0) * rho, gp = ((k & 1) ? -g : g) * rho;
+            const float ws = (k & 2) ? -sig : sig;
+            sm.sN[buf][i] = make_float4(f0p, f0p, -gp, -gp);
+            sm.sWn[buf][i] = make_float4(wr * ws, wr * ws, wi * ws, wi * ws);
         }
     }
-    ff xe{__shfl_up_sync(0xffffffffu, pe.hi, 1), __shfl_up_sync(0xffffffffu, pe.lo, 1)};
-    ff xo{__shfl_up_sync(0xffffffffu, po.hi, 1), __shfl_up_sync(0xffffffffu, po.lo, 1)};
-    if (lane == 0) xe = xo = ff{1.0f, 0.0f};
-    const float4 carry = sm.sSig;
-    ff se = ff_mul(ff{carry.z, carry.w}, xe);  // sigma at the lane's first entry (even)
-    ff so = ff_mul(ff{carry.x, carry.y}, xo);  // sigma at the entry before it (odd)
-#pragma unroll
-    for (int q = 0; q < EPL; ++q) {
-        const int e = e0 + q;
-        const float4 r = sm.sRaw[e];
-        const ff f = (e < nl) ? ff{r.z, r.w} : ff{1.0f, 0.0f};
-        float s_e, s_n;  // sigma_e, sigma_{e+1}
-        if (q & 1) {
-            s_e = so.hi;
-            se = ff_mul(se, f);
-            s_n = se.hi;
-        } else {
-            s_e = se.hi;
-            so = ff_mul(so, f);
-            s_n = so.hi;
-        }
-        const float4 w = sm.sW[buf][e];
-        const float rho = __fdividef(s_e, s_n);  // a float coefficient's accuracy suffices
-        const float f0p = r.x * rho, gp = r.y * rho;
-        const float wr = w.x * s_e, wi = w.z * s_e;
-        sm.sN[e] = (e < nl) ? make_float4(f0p, f0p, -gp, -gp) : make_float4(0.f, 0.f, 0.f, 0.f);
-        sm.sWn[e] = (e < nl) ? make_float4(wr, wr, wi, wi) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    // carry: sigma at the tile's last two entries (lane 31: so = sigma_{TL-1}, se = sigma_{TL})
-    __syncwarp();
-    if (lane == 31) sm.sSig = make_float4(so.hi, so.lo, se.hi, se.lo);
 }
 
 // the K pair of each chain pair at tile entry i: the thread's common K (UNIFORM: all its
@@ -405,12 +440,20 @@ __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, c
     } else {
         static_assert(RESCALE_EVERY == 4, "the masked loop below is unrolled by four");
         for (; i + 3 < nl; i += 4) {
+            if (warp_terms_live(sp)) {
 #pragma unroll
-            for (int q = 0; q < 4; q += 2) {
-                k_pairs<NP, UNIFORM>(sK[i + q], thigh, hbits, kp);
-                step_pairs<NP, 0, true>(sA[i + q], kp, sW[i + q], x2p, cur, aux, sp, pr, pi);
-                k_pairs<NP, UNIFORM>(sK[i + q + 1], thigh, hbits, kp);
-                step_pairs<NP, 1, true>(sA[i + q + 1], kp, sW[i + q + 1], x2p, cur, aux, sp, pr, pi);
+                for (int q = 0; q < 4; q += 2) {
+                    k_pairs<NP, UNIFORM>(sK[i + q], thigh, hbits, kp);
+                    step_pairs<NP, 0, true>(sA[i + q], kp, sW[i + q], x2p, cur, aux, sp, pr, pi);
+                    k_pairs<NP, UNIFORM>(sK[i + q + 1], thigh, hbits, kp);
+                    step_pairs<NP, 1, true>(sA[i + q + 1], kp, sW[i + q + 1], x2p, cur, aux, sp, pr, pi);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    k_pairs<NP, UNIFORM>(sK[i + q], thigh, hbits, kp);
+                    step_pairs_rec<NP>(sA[i + q], kp, x2p, cur, aux);
+                }
             }
             rescale_pairs(cur, aux, nsc, sp);
         }
@@ -445,10 +488,15 @@ __device__ __forceinline__ void tile_steps_norm(const float4 *sN, const float4 *
         if (i < nl) step_norm<NP, 0, false>(sN[i], sWn[i], cbp, cur, aux, sp, pr, pi);
     } else {
         for (; i + 3 < nl; i += 4) {
+            if (warp_terms_live(sp)) {
 #pragma unroll
-            for (int q = 0; q < 4; q += 2) {
-                step_norm<NP, 0, true>(sN[i + q], sWn[i + q], cbp, cur, aux, sp, pr, pi);
-                step_norm<NP, 1, true>(sN[i + q + 1], sWn[i + q + 1], cbp, cur, aux, sp, pr, pi);
+                for (int q = 0; q < 4; q += 2) {
+                    step_norm<NP, 0, true>(sN[i + q], sWn[i + q], cbp, cur, aux, sp, pr, pi);
+                    step_norm<NP, 1, true>(sN[i + q + 1], sWn[i + q + 1], cbp, cur, aux, sp, pr, pi);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) step_norm_rec<NP>(sN[i + q], cbp, cur, aux);
             }
             rescale_pairs(cur, aux, nsc, sp);
         }
@@ -481,7 +529,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
     const int MB1 = A.mb_max + 1;
     const int L = A.l_max;
     const int NB = A.n_beta;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     // a thread's chains are CPT adjacent angles, a warp's 32 CPT consecutive ones, so that
     // only the warps that hold angles near a pole take the difference form
     const int j0 = chunk * NT * CPT + tid * CPT;  // angle of chain c: j0 + c
@@ -522,7 +570,12 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
         const int ms = k / MB1, mb = k - ms * MB1;
         const int l0 = mb > ms ? mb : ms;
         const bool norm = wbulk && l0 < NORM_L0_LIMIT;  // this warp runs the normalised form
-        const bool need_norm = __syncthreads_or(norm) != 0;
+        if (tid == 0) {  // read by build_tile after the barrier below
+            const ff k0 = sigma_log(l0, mb, ms, T.E_f), k1 = sigma_log(l0 + 1, mb, ms, T.E_f);
+            sm.sKc = make_float4(k0.hi, k0.lo, k1.hi, k1.lo);
+        }
+        const int n_norm = __syncthreads_count(norm);  // warp-uniform: a warp runs one form
+        const bool need_norm = n_norm > 0, need_diff = n_norm < NT;
 
         float2 cur[NP], aux[NP], sp[NP], pr[2][NP], pi[2][NP];
         float2 xv[NP];  // per chain: cos(beta) (normalised form) or x^2 (difference form)
@@ -560,16 +613,10 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
             sm.sAcc[c][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         bool warp_plain = false;
-        if (tid == 0) sm.sSig = make_float4(1.0f, 0.0f, 1.0f, 0.0f);  // sigma_{l0-1} (entered as 1), sigma_{l0}
 
         // first tile's operands into buffer 0
-        for (int i = tid; i < TL; i += NT)
-            if (l0 + i <= L) build_tile_entry<NT, CPT, TL>(A, T, l0 + i, l0, mb, ms, sm, 0, i);
+        build_tile<NT, CPT, TL>(A, T, l0, l0, mb, ms, need_diff, need_norm, sm, 0);
         __syncthreads();
-        if (need_norm) {
-            if (tid < 32) normalise_tile<NT, CPT, TL>(sm, 0, min(TL, L + 1 - l0), lane);
-            __syncthreads();
-        }
 
         int buf = 0;
         for (int ts = l0; ts <= L; ts += TL, buf ^= 1) {
@@ -599,7 +646,7 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 warp_plain = __all_sync(0xffffffffu, p);
             }
             if (norm)
-                tile_steps_norm<NP, TL>(sm.sN, sm.sWn, nl, warp_plain, xv, cur, aux, nsc, sp, pr, pi);
+                tile_steps_norm<NP, TL>(sm.sN[buf], sm.sWn[buf], nl, warp_plain, xv, cur, aux, nsc, sp, pr, pi);
             else if (uniform)
                 tile_steps<NP, TL, true>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hbits, xv, cur,
                                          aux, nsc, sp, pr, pi);
@@ -622,17 +669,12 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 sm.sAcc[c][tid] = acc;
             }
             // the next tile: its operands into the other buffer (their previous readers
-            // passed the barrier at the end of the last tile), a barrier, then the
-            // normalised form's operands (one warp) and a second barrier
+            // passed the barrier at the end of the last tile) as soon as this warp is done
+            // with the current one, then the tile's one barrier
             const int tn = ts + TL;
             if (tn <= L) {
-                for (int i = tid; i < TL; i += NT)
-                    if (tn + i <= L) build_tile_entry<NT, CPT, TL>(A, T, tn + i, l0, mb, ms, sm, buf ^ 1, i);
+                build_tile<NT, CPT, TL>(A, T, tn, l0, mb, ms, need_diff, need_norm, sm, buf ^ 1);
                 __syncthreads();
-                if (need_norm) {
-                    if (tid < 32) normalise_tile<NT, CPT, TL>(sm, buf ^ 1, min(TL, L + 1 - tn), lane);
-                    __syncthreads();
-                }
             }
         }
         double2 *out = reinterpret_cast<double2 *>(A.c_out) + ((size_t)mb * (A.ms_max + 1) + ms) * NB;
@@ -644,8 +686,12 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 const float4 acc = sm.sAcc[c][tid];
                 const double sg = (!norm && (fl & 2) && (l0 & 1)) ? -1.0 : 1.0;
                 const double nan = __longlong_as_double(0x7ff8000000000000LL);
-                const double re = sg * ((double)acc.x + (double)acc.y);
-                const double im = sg * ((double)acc.z + (double)acc.w);
+                // the weights' power-of-two scales back (two exact factors within the
+                // double range)
+                const int k = (A.ea ? A.ea[ms] : 0) + (A.eb ? A.eb[mb] : 0);
+                const int k1 = min(1023, max(-1022, k / 2)), k2 = min(1023, max(-1022, k - k1));
+                const double re = sg * ((((double)acc.x + (double)acc.y) * pow2(k1)) * pow2(k2));
+                const double im = sg * ((((double)acc.z + (double)acc.w) * pow2(k1)) * pow2(k2));
                 out[j] = (fl & 1) ? make_double2(nan, nan) : make_double2(re, im);
                 n_elem += (unsigned long long)(L + 1 - l0);
             }

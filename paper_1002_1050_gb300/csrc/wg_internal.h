@@ -50,6 +50,9 @@ struct ConvArgs {
     int k_lo = 0, k_hi = -1;  // chain columns k = ms (mb_max + 1) + mb in [k_lo, k_hi); k_hi < 0: all
     double offset = 0.0;      // the l_min cut's offset (kernels built with the cut only)
     int wait_tries = WG_WAIT_TRIES_DEFAULT;  // tries of each TMA wait before it gives up
+    // FP32 form only: per-column power-of-two weight scales, a[l][ms] 2^-ea[ms] and
+    // b[l][mb] 2^-eb[mb] below 1 in magnitude (null: unscaled)
+    const int *ea = nullptr, *eb = nullptr;
 };
 
 struct DTableBwdArgs {

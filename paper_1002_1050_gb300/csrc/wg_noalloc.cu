@@ -173,7 +173,7 @@ extern "C" int wigner_conv_sum_noalloc(int l_max, int mb_max, int ms_max, int n_
     t.Q = tab + 3 * kN2;
     t.R1 = tab + 4 * kN2;
     t.R2 = tab + 4 * kN2 + kN1;
-    t.lnf_f = t.P_f = t.Q_f = t.R1_f = t.R2_f = nullptr;  // used only by the FP32 form
+    t.lnf_f = t.P_f = t.Q_f = t.R1_f = t.R2_f = t.E_f = nullptr;  // used only by the FP32 form
     t.lcap = kLcap;
     t.status = status;  // read by wigner_noalloc_status
     wg::ConvArgs ca{l_max, mb_max, ms_max, n_beta, beta, (const double *)a, (const double *)b, (double *)c_out,

@@ -116,6 +116,15 @@ except W.WignerError as e:
     out.append(e.code)
 C = W.wigner_conv_sum(tb, ta, tbm).cpu().numpy()  # retry: allocates and computes
 out.append(float(np.max(np.abs(C - O.conv_sum(L, MB, MS, beta, a, b)))))
+# the FP32 form's stream-ordered scratch (its weight scales)
+W.debug_inject_alloc_failures(1)
+try:
+    W.wigner_conv_sum(tb, ta, tbm, form='fp32x'); out.append('no error')
+except W.WignerError as e:
+    out.append(e.code)
+C = W.wigner_conv_sum(tb, ta, tbm, form='fp32x').cpu().numpy()
+ref = O.conv_sum(L, MB, MS, beta, a, b)
+out.append(float(np.linalg.norm((C - ref).ravel()) / np.linalg.norm(ref.ravel())))
 # the adjoint's workspace
 G = torch.ones((MB + 1, MS + 1, NB), dtype=torch.complex128, device='cuda')
 Ct = W.wigner_conv_sum(tb, ta, tbm)
@@ -137,7 +146,8 @@ def test_injected_allocation_failures_fresh_process(W):
     res = eval(line[len("RESULT"):])
     assert res[0] == WG_ERR_ALLOC and res[1] == WG_ERR_ALLOC, res
     assert res[2] <= 1e-11, res
-    assert res[3] == WG_ERR_ALLOC and res[4] == 0, res
+    assert res[3] == WG_ERR_ALLOC and res[4] <= 1e-4, res
+    assert res[5] == WG_ERR_ALLOC and res[6] == 0, res
 
 
 SENT = 1.2345678e300  # a value no kernel writes

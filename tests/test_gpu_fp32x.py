@@ -72,6 +72,29 @@ def test_conv_fp32x_small(W, L, MB, MS, NB):
     assert np.all(np.isfinite(C))
 
 
+def test_conv_fp32x_weights_outside_float_range(W):
+    """Columns whose weights lie far outside float's range (a sky column scaled by 1e-80,
+    beam orders by 1e-70 and 1e+60): each non-zero column of C keeps its relative accuracy, as the
+    weights enter the float recursion with a per-column power-of-two scale."""
+    L, MB, MS, NB = 300, 4, 300, 257
+    beta = I.beta_gauss_legendre(NB)[0]
+    a = I.sky_alm(L, MS, 21)
+    b = I.beam_blm(L, MB, fwhm=0.03)
+    a[:, 7] *= 1e-80
+    b[:, 2] *= 1e-70
+    b[:, 4] *= 1e60
+    C = W.wigner_conv_sum(_cuda(beta), _cuda(a), _cuda(b), form="fp32x").cpu().numpy()
+    W.check_device_status()
+    ref = O.conv_sum(L, MB, MS, beta, a, b)
+    assert np.all(np.isfinite(C))
+    for mb in range(MB + 1):
+        for ms in (0, 7, 150, 300):
+            if not np.any(ref[mb, ms]):  # the beam's odd orders are zero
+                assert not np.any(C[mb, ms]), (mb, ms)
+            else:
+                assert _rel_l2(C[mb, ms], ref[mb, ms]) <= 1e-4, (mb, ms)
+
+
 def test_conv_fp32x_unsorted_angles_with_poles(W):
     """Angles in random order, both poles and pi/2 included: threads hold chains on both
     sides of pi/2 (each chain picks its own K coefficient) and scaled and plain chains

@@ -152,3 +152,30 @@ def test_noalloc_status_word(lib):
         assert _call_noalloc(raw, L, MB, MS, beta, a, b, out) == 0
         assert raw.wigner_noalloc_status(stream) == 0
         assert float((out - ref).abs().max()) <= TOL
+
+
+def test_noalloc_captured_in_cuda_graph(lib):
+    """A call captured into a CUDA graph (after the per-device set-up of an earlier call):
+    the capture succeeds, as it would not if the call allocated or synchronised, and the
+    replayed graph matches wigner_conv_sum."""
+    W, raw = lib
+    L, MB, MS, NB = 210, 5, 210, 333
+    beta = _cuda(I.beta_gauss_legendre(NB)[0])
+    a = _cuda(I.sky_alm(L, MS, 11))
+    b = _cuda(I.beam_blm(L, MB, fwhm=0.04))
+    ref = W.wigner_conv_sum(beta, a, b)
+    W.check_device_status()
+    out = torch.zeros((MB + 1, MS + 1, NB), dtype=torch.complex128, device="cuda")
+    assert _call_noalloc(raw, L, MB, MS, beta, a, b, out) == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rc = _call_noalloc(raw, L, MB, MS, beta, a, b, out)
+    assert rc == 0, raw.wigner_last_error_message()
+    out.fill_(complex(math.nan, math.nan))
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert float((out - ref).abs().max()) <= TOL
+    assert raw.wigner_noalloc_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
