@@ -547,7 +547,14 @@ def _dtable_block(W, dev, stream, args):
             ref64 = out.clone()
         else:
             res["fp32x_max_abs_diff_vs_fp64_table"] = float((out - ref64).abs().max())
-            del ref64
+            # the FP32 form's seeds (float-float logarithm, float value): relative error of
+            # d^{l0} against the FP64 table, over seeds of magnitude above 1e-30
+            l0 = torch.maximum(torch.arange(MB + 1, device=dev)[:, None], torch.arange(MS + 1, device=dev)[None, :])
+            idx = l0[:, :, None, None].expand(MB + 1, MS + 1, 1, beta.numel())
+            s32, s64 = out.gather(2, idx), ref64.gather(2, idx)
+            big = s64.abs() > 1e-30
+            res["fp32x_seed_max_rel_err"] = float(((s32 - s64).abs()[big] / s64.abs()[big]).max())
+            del ref64, s32, s64, idx, big
         times = []
         for _ in range(args.dtable_steps):
             flush.fill_(1)

@@ -21,8 +21,9 @@
 //  * Sum C = sum_l w_l d^l in float: terms go into two per-parity partial sums
 //    (even/odd l, so the (-1)^l of the mirrored chains is applied once per tile), and
 //    each tile's partials are added into a Neumaier-compensated float accumulator.
-//    Terms start once the value reaches 2^-64 (the paper's 1e-30 skip of Sec. 4.2.1
-//    drops terms below the FP32 form's resolution anyway).
+//    Terms start once the value reaches 2^-128 (below it their factor 2^(64 n) is 0;
+//    the paper's 1e-30 skip of Sec. 4.2.1 drops terms below the FP32 form's resolution
+//    anyway), and a warp whose chains are all below it steps without the sum.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -52,6 +52,26 @@ def test_dtable_small_ragged(W, L, MB, MS, NB):
     assert np.max(np.abs(d - ref)) <= TOL
 
 
+def test_dtable_long_columns_and_poles(W):
+    """Columns past l0 = 1024 and angles next to the poles, where the seed's logarithm is
+    large, against the oracle's chains at the FP64 bar; also more angle chunks (40
+    angles: a full and a ragged 32-angle chunk).  (Near the poles Eq. lrec's two roots
+    merge and two double-precision evaluations of a chain drift apart like l^2 times
+    the rounding unit: about 1e-11 at l = 1500, 6e-12 at l = 1100.)"""
+    L, MB, MS = 1100, 16, 1100
+    beta = np.concatenate([[0.0, 1e-4, 2e-3, math.pi / 2, math.pi - 2e-3, math.pi - 1e-4, math.pi],
+                           I.beta_uniform(33, 1e-3, math.pi - 1e-3, 8)])
+    d = W.wigner_d_table(_cuda(beta), L, MB, MS)
+    W.check_device_status()
+    for mb, ms in [(0, 0), (16, 16), (3, 700), (16, 1030), (5, 1050), (16, 1099), (0, 1100), (11, 1024),
+                   (7, 1025)]:
+        ref = O.d_column(L, mb, ms, beta)
+        got = d[mb, ms].cpu().numpy()
+        assert float(np.max(np.abs(got - ref))) <= TOL, (mb, ms)
+    del d
+    torch.cuda.empty_cache()
+
+
 def test_dtable_counters(W):
     L, MB, MS, beta, _, _ = I.make_config("dtable_l256")
     cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
