@@ -703,7 +703,8 @@ def _multi_block(W, dev, stream, args, beta, b, n_elem, n_sum, mean_ms):
                                              "note": "bf16 slice products issued by tcgen05.mma (42 per 32-order "
                                                      "tile and 32 skies) over the measured cuBLAS bf16 peak; the "
                                                      "launch is bound by the FP64 recursion, not the tensor pipe"},
-                                  "fp64_recursion_tflops": 5 * n_elem / (ms_tc / 1e3) / 1e12}}
+                                  "fp64_recursion_tflops": 5 * n_elem * ((K_TC + 31) // 32) / (ms_tc / 1e3) / 1e12,
+                                  "fp64_recursion_note": "one recursion per launch column group of 32 skies"}}
 
 
 def _matrix_block(W, dev, stream, args):

@@ -7,9 +7,11 @@
 
 namespace wg {
 
+// shared memory in the dynamic segment (a CTA of 256 threads needs more than 48 KB)
 template <int NT, int CPT, int TL>
-__global__ void __launch_bounds__(NT, 6) conv_fp32x_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
-    __shared__ SmemFp32<NT, CPT, TL> sm;
+__global__ void __launch_bounds__(NT, 768 / NT) conv_fp32x_kernel(ConvArgs A, Tables T, int n_chunks, int group) {
+    extern __shared__ __align__(16) unsigned char fp32x_smem[];
+    SmemFp32<NT, CPT, TL> &sm = *reinterpret_cast<SmemFp32<NT, CPT, TL> *>(fp32x_smem);
     const int item = blockIdx.x;
     const int chunk = item % n_chunks;
     const int grp = item / n_chunks;
@@ -67,8 +69,11 @@ static int launch_conv_fp32x_t(const ConvArgs &a_in, const Tables &t, void *stre
     fp32x_scales_kernel<<<(unsigned)((n_sc + 127) / 128), 128, 0, s>>>(a.a, a.b, a.l_max, a.mb_max, a.ms_max,
                                                                        const_cast<int *>(a.ea), const_cast<int *>(a.eb));
     e = cudaGetLastError();
+    constexpr size_t smem = sizeof(SmemFp32<NT, CPT, TL>);
+    if (e == cudaSuccess && smem > 48 * 1024)  // an attribute of the current device's function
+        e = cudaFuncSetAttribute(conv_fp32x_kernel<NT, CPT, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        conv_fp32x_kernel<NT, CPT, TL><<<(unsigned)items, NT, 0, s>>>(a, t, n_chunks, group);
+        conv_fp32x_kernel<NT, CPT, TL><<<(unsigned)items, NT, smem, s>>>(a, t, n_chunks, group);
         e = cudaGetLastError();
     }
     const cudaError_t ef = cudaFreeAsync(sc, s);
@@ -76,7 +81,7 @@ static int launch_conv_fp32x_t(const ConvArgs &a_in, const Tables &t, void *stre
 }
 
 int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream) {
-    return launch_conv_fp32x_t<128, 4, 120>(a, t, stream, 16);
+    return launch_conv_fp32x_t<256, 4, 240>(a, t, stream, 16);
 }
 
 // ---------------------------------------------------------------------------
