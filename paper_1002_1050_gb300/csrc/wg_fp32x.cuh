@@ -236,14 +236,16 @@ __device__ __forceinline__ bool warp_terms_live(const float2 (&sp)[NP]) {
     return __any_sync(0xffffffffu, any);
 }
 
-// Rescaling of one scaled chain, run every RESCALE_EVERY steps of a masked tile: a
-// mantissa at or above 2^64 is scaled by 2^-64 (n += 1), one of a scaled chain below
-// 2^-64 by 2^64 (n -= 1), jointly with aux; then sp = 2^(64 n) (0 for n <= -2).  No
-// branch.  Between two calls the mantissa changes by less than 2^60: the ratio of
-// consecutive values is at most |F0 (cos b - F1)| + 1 <= 2 (l0 + 1) / (k + 1) + 1 at
-// l = l0 + k (largest for m_b = m_sky = l0), so four steps from l0 <= 32767 grow it by
-// at most 2^64 / 24, and a mantissa left in [2^-64, 2^64) stays a normal float.
-constexpr int RESCALE_EVERY = 4;
+// Rescaling of one scaled chain, run every 4 or 8 steps of a masked tile: a mantissa at
+// or above 2^64 is scaled by 2^-64 (n += 1), one of a scaled chain below 2^-64 by 2^64
+// (n -= 1), jointly with aux; then sp = 2^(64 n) (0 for n <= -2).  No branch.  Between
+// two calls the mantissa changes by less than 2^60: the ratio of consecutive values is
+// at most |F0 (cos b - F1)| + 1 <= 2 (l0 + 1) / (k + 1) + 1 at l = l0 + k (largest for
+// m_b = m_sky = l0; 4 (l0 + 1) / (k + 1) + 1 in the normalised form, whose rho <= 2),
+// so four steps from any l0 <= 32767 grow it by at most 2^64 / 24, and eight steps grow
+// it by at most 181^8 < 2^60 once k >= (l0 + 1) / 45 (rescale_period); a mantissa left
+// in [2^-64, 2^64) stays a normal float.
+__host__ __device__ __forceinline__ int rescale_period(int l0, int k) { return 45 * k >= l0 + 1 ? 8 : 4; }
 __device__ __forceinline__ void rescale32(float &cur, float &aux, int &n, float &sp) {
     const float m = fabsf(cur);
     const bool dn = m >= 0x1p64f;
@@ -422,7 +424,7 @@ __device__ __forceinline__ void k_pairs(const float4 &k4, int thigh, int hbits, 
 // The steps of one l-tile (nl orders) in the difference form for every chain of the thread.
 template <int NP, int TL, bool UNIFORM>
 __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, const float4 *sW, int nl, bool plain,
-                                           int thigh, int hbits, const float2 (&x2p)[NP],
+                                           int period, int thigh, int hbits, const float2 (&x2p)[NP],
                                            float2 (&cur)[NP], float2 (&aux)[NP], int (&nsc)[2 * NP],
                                            float2 (&sp)[NP], float2 (&pr)[2][NP], float2 (&pi)[2][NP]) {
     float2 kp[NP];
@@ -439,7 +441,27 @@ __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, c
             step_pairs<NP, 0, false>(sA[i], kp, sW[i], x2p, cur, aux, sp, pr, pi);
         }
     } else {
-        static_assert(RESCALE_EVERY == 4, "the masked loop below is unrolled by four");
+        // groups of 8 steps between rescales where rescale_period allows, else of 4
+        if (period == 8) {
+            for (; i + 7 < nl; i += 8) {
+                if (warp_terms_live(sp)) {
+#pragma unroll
+                    for (int q = 0; q < 8; q += 2) {
+                        k_pairs<NP, UNIFORM>(sK[i + q], thigh, hbits, kp);
+                        step_pairs<NP, 0, true>(sA[i + q], kp, sW[i + q], x2p, cur, aux, sp, pr, pi);
+                        k_pairs<NP, UNIFORM>(sK[i + q + 1], thigh, hbits, kp);
+                        step_pairs<NP, 1, true>(sA[i + q + 1], kp, sW[i + q + 1], x2p, cur, aux, sp, pr, pi);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        k_pairs<NP, UNIFORM>(sK[i + q], thigh, hbits, kp);
+                        step_pairs_rec<NP>(sA[i + q], kp, x2p, cur, aux);
+                    }
+                }
+                rescale_pairs(cur, aux, nsc, sp);
+            }
+        }
         for (; i + 3 < nl; i += 4) {
             if (warp_terms_live(sp)) {
 #pragma unroll
@@ -476,7 +498,7 @@ __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, c
 
 // The steps of one l-tile in the normalised form ((cur, aux) hold (u^l, u^{l-1})).
 template <int NP, int TL>
-__device__ __forceinline__ void tile_steps_norm(const float4 *sN, const float4 *sWn, int nl, bool plain,
+__device__ __forceinline__ void tile_steps_norm(const float4 *sN, const float4 *sWn, int nl, bool plain, int period,
                                                 const float2 (&cbp)[NP], float2 (&cur)[NP], float2 (&aux)[NP],
                                                 int (&nsc)[2 * NP], float2 (&sp)[NP], float2 (&pr)[2][NP],
                                                 float2 (&pi)[2][NP]) {
@@ -488,6 +510,21 @@ __device__ __forceinline__ void tile_steps_norm(const float4 *sN, const float4 *
         }
         if (i < nl) step_norm<NP, 0, false>(sN[i], sWn[i], cbp, cur, aux, sp, pr, pi);
     } else {
+        if (period == 8) {
+            for (; i + 7 < nl; i += 8) {
+                if (warp_terms_live(sp)) {
+#pragma unroll
+                    for (int q = 0; q < 8; q += 2) {
+                        step_norm<NP, 0, true>(sN[i + q], sWn[i + q], cbp, cur, aux, sp, pr, pi);
+                        step_norm<NP, 1, true>(sN[i + q + 1], sWn[i + q + 1], cbp, cur, aux, sp, pr, pi);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) step_norm_rec<NP>(sN[i + q], cbp, cur, aux);
+                }
+                rescale_pairs(cur, aux, nsc, sp);
+            }
+        }
         for (; i + 3 < nl; i += 4) {
             if (warp_terms_live(sp)) {
 #pragma unroll
@@ -646,13 +683,15 @@ __device__ __forceinline__ void conv_fp32x_item(const ConvArgs &A, const Tables 
                 }
                 warp_plain = __all_sync(0xffffffffu, p);
             }
+            const int period = rescale_period(l0, ts - l0);
             if (norm)
-                tile_steps_norm<NP, TL>(sm.sN[buf], sm.sWn[buf], nl, warp_plain, xv, cur, aux, nsc, sp, pr, pi);
+                tile_steps_norm<NP, TL>(sm.sN[buf], sm.sWn[buf], nl, warp_plain, period, xv, cur, aux, nsc, sp, pr,
+                                        pi);
             else if (uniform)
-                tile_steps<NP, TL, true>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hbits, xv, cur,
+                tile_steps<NP, TL, true>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, period, thigh, hbits, xv, cur,
                                          aux, nsc, sp, pr, pi);
             else
-                tile_steps<NP, TL, false>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, thigh, hbits, xv, cur,
+                tile_steps<NP, TL, false>(sm.sA[buf], sm.sK[buf], sm.sW[buf], nl, warp_plain, period, thigh, hbits, xv, cur,
                                           aux, nsc, sp, pr, pi);
             // partials of this tile into the compensated sums; the sign of the odd-offset
             // partial is (-1) for mirrored chains of the difference form, and the tile's
