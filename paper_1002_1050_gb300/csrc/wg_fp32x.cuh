@@ -242,10 +242,13 @@ __device__ __forceinline__ bool warp_terms_live(const float2 (&sp)[NP]) {
 // two calls the mantissa changes by less than 2^60: the ratio of consecutive values is
 // at most |F0 (cos b - F1)| + 1 <= 2 (l0 + 1) / (k + 1) + 1 at l = l0 + k (largest for
 // m_b = m_sky = l0; 4 (l0 + 1) / (k + 1) + 1 in the normalised form, whose rho <= 2),
-// so four steps from any l0 <= 32767 grow it by at most 2^64 / 24, and eight steps grow
-// it by at most 181^8 < 2^60 once k >= (l0 + 1) / 45 (rescale_period); a mantissa left
-// in [2^-64, 2^64) stays a normal float.
-__host__ __device__ __forceinline__ int rescale_period(int l0, int k) { return 45 * k >= l0 + 1 ? 8 : 4; }
+// so four steps from any l0 <= 32767 grow it by at most 2^64 / 24, eight steps by at
+// most 181^8 < 2^60 once k >= (l0 + 1) / 45, and sixteen steps of the normalised form by
+// at most 13^16 < 2^60 once k >= (l0 + 1) / 3 (rescale_period; the difference form keeps
+// groups of at most 8); a mantissa left in [2^-64, 2^64) stays a normal float.
+__host__ __device__ __forceinline__ int rescale_period(int l0, int k) {
+    return 3 * k >= l0 + 1 ? 16 : (45 * k >= l0 + 1 ? 8 : 4);
+}
 __device__ __forceinline__ void rescale32(float &cur, float &aux, int &n, float &sp) {
     const float m = fabsf(cur);
     const bool dn = m >= 0x1p64f;
@@ -442,7 +445,7 @@ __device__ __forceinline__ void tile_steps(const float4 *sA, const float4 *sK, c
         }
     } else {
         // groups of 8 steps between rescales where rescale_period allows, else of 4
-        if (period == 8) {
+        if (period >= 8) {
             for (; i + 7 < nl; i += 8) {
                 if (warp_terms_live(sp)) {
 #pragma unroll
@@ -510,7 +513,22 @@ __device__ __forceinline__ void tile_steps_norm(const float4 *sN, const float4 *
         }
         if (i < nl) step_norm<NP, 0, false>(sN[i], sWn[i], cbp, cur, aux, sp, pr, pi);
     } else {
-        if (period == 8) {
+        if (period == 16) {
+            for (; i + 15 < nl; i += 16) {
+                if (warp_terms_live(sp)) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2) {
+                        step_norm<NP, 0, true>(sN[i + q], sWn[i + q], cbp, cur, aux, sp, pr, pi);
+                        step_norm<NP, 1, true>(sN[i + q + 1], sWn[i + q + 1], cbp, cur, aux, sp, pr, pi);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) step_norm_rec<NP>(sN[i + q], cbp, cur, aux);
+                }
+                rescale_pairs(cur, aux, nsc, sp);
+            }
+        }
+        if (period >= 8) {
             for (; i + 7 < nl; i += 8) {
                 if (warp_terms_live(sp)) {
 #pragma unroll
