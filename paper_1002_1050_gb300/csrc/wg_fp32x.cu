@@ -87,8 +87,32 @@ int launch_conv_fp32x(const ConvArgs &a, const Tables &t, void *stream) {
 // ---------------------------------------------------------------------------
 // d-table, FP32 form (values stored as double)
 // ---------------------------------------------------------------------------
+// the angles' quantities of the FP32 form, once per launch (one thread per angle)
+__global__ void angle32_setup_kernel(const double *beta, int n_beta, Angle32 *ang, int *status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_beta) return;
+    const Angle32 t = make_angle32(beta[j]);
+    if (t.bad) raise_status(status, WG_DEVERR_BETA);
+    ang[j] = t;
+}
+
+// mant 2^(64 n) (times -1 if neg) as a double by integer operations on the float's bits:
+// exact while the result is a normal double; below 2^-1022, and for a zero or subnormal
+// float, 0
+__device__ __forceinline__ double f32_scaled_to_double(float mant, int n, bool neg) {
+    const unsigned u = __float_as_uint(mant) ^ (neg ? 0x80000000u : 0u);
+    const int e = (int)((u >> 23) & 0xffu);
+    const int ed = e - 127 + 1023 + 64 * n;  // the double's biased exponent
+    if (e == 0 || ed <= 0) return 0.0;
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                            ((unsigned long long)ed << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// One CTA per (column, NT angles), one chain per thread; the column's difference-form
+// coefficients of each l-tile built once per CTA in shared memory.
 template <int NT, int TL>
-__global__ void __launch_bounds__(NT) dtable_fp32x_kernel(DTableArgs A, Tables T) {
+__global__ void __launch_bounds__(NT) dtable_fp32x_kernel(DTableArgs A, Tables T, const Angle32 *ang) {
     const int col = blockIdx.x;
     const int mb = col / (A.ms_max + 1), ms = col % (A.ms_max + 1);
     const int j = blockIdx.y * NT + threadIdx.x;
@@ -99,9 +123,7 @@ __global__ void __launch_bounds__(NT) dtable_fp32x_kernel(DTableArgs A, Tables T
     double *out = A.d_out + (size_t)col * (size_t)(L + 1) * NB;
     if (valid)
         for (int l = 0; l < l0; ++l) out[(size_t)l * NB + j] = 0.0;
-    const double beta = valid ? A.beta[j] : 1.0;
-    const Angle32 t = make_angle32(beta);
-    if (valid && t.bad) raise_status(T.status, WG_DEVERR_BETA);
+    const Angle32 t = ang[valid ? j : 0];
     const bool high = t.high;
     const float x2 = t.x2;
     const Seed32 sd = seed32(mb, ms, t, T);
@@ -120,12 +142,9 @@ __global__ void __launch_bounds__(NT) dtable_fp32x_kernel(DTableArgs A, Tables T
         const int nl = min(TL, L + 1 - ts);
         for (int i = 0; i < nl; ++i) {
             const int l = ts + i;
-            if (valid) {
-                double v = (double)cur;
-                if (n != 0) v = scalbn(v, 64 * n);
-                if (high && (l & 1)) v = -v;
-                out[(size_t)l * NB + j] = t.bad ? __longlong_as_double(0x7ff8000000000000LL) : v;
-            }
+            if (valid)
+                out[(size_t)l * NB + j] = t.bad ? __longlong_as_double(0x7ff8000000000000LL)
+                                                : f32_scaled_to_double(cur, n, high && (l & 1));
             const float4 tc = sT[i];
             const float coef = fmaf(tc.x, x2, high ? tc.w : tc.z);
             aux = fmaf(tc.y, aux, coef * cur);
@@ -142,10 +161,23 @@ __global__ void __launch_bounds__(NT) dtable_fp32x_kernel(DTableArgs A, Tables T
 int launch_dtable_fp32x(const DTableArgs &a, const Tables &t, void *stream) {
     constexpr int NT = 64, TL = 128;
     if (a.n_beta == 0) return 0;
-    const int ncol = (a.mb_max + 1) * (a.ms_max + 1);
-    dim3 grid(ncol, (a.n_beta + NT - 1) / NT);
-    dtable_fp32x_kernel<NT, TL><<<grid, NT, 0, (cudaStream_t)stream>>>(a, t);
-    return (int)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemPool_t pool;
+    if (host_pool(&pool) != WG_OK) return (int)cudaErrorMemoryAllocation;
+    Angle32 *ang = nullptr;
+    cudaError_t e = alloc_injected() ? cudaErrorMemoryAllocation
+                                     : cudaMallocFromPoolAsync((void **)&ang, (size_t)a.n_beta * sizeof(Angle32), pool, s);
+    if (e != cudaSuccess) return (int)e;
+    angle32_setup_kernel<<<(a.n_beta + 127) / 128, 128, 0, s>>>(a.beta, a.n_beta, ang, t.status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        const int ncol = (a.mb_max + 1) * (a.ms_max + 1);
+        dim3 grid(ncol, (a.n_beta + NT - 1) / NT);
+        dtable_fp32x_kernel<NT, TL><<<grid, NT, 0, s>>>(a, t, ang);
+        e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(ang, s);
+    return (int)(e != cudaSuccess ? e : ef);
 }
 
 }  // namespace wg
