@@ -185,6 +185,21 @@ __device__ __forceinline__ void ff_mac2(float2 &hi, float2 &lo, float2 wh, float
     hi = h2;
 }
 
+// (x.hi, x.lo) += (y.hi, y.lo) in float-float for a pair of values with the packed f32x2
+// instructions: per lane the steps of ff_add (TwoSum, then Fast2Sum), a - b written
+// fma(b, -1, a) (one rounding, as a subtraction)
+__device__ __forceinline__ void ff_add2(float2 &xh, float2 &xl, float2 yh, float2 yl) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(xh, yh);
+    const float2 bb = __ffma2_rn(xh, m1, s);                         // s - xh
+    const float2 t1 = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, xh);     // xh - (s - bb)
+    const float2 e = __fadd2_rn(t1, __ffma2_rn(bb, m1, yh));         // + (yh - bb)
+    const float2 e2 = __fadd2_rn(e, __fadd2_rn(xl, yl));
+    const float2 h = __fadd2_rn(s, e2);
+    xl = __ffma2_rn(__ffma2_rn(s, m1, h), m1, e2);                   // e2 - (h - s)
+    xh = h;
+}
+
 // ---------------------------------------------------------------------------
 // exponent-field helpers
 // ---------------------------------------------------------------------------

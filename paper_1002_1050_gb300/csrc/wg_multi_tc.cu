@@ -511,17 +511,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tmem_ld8(tl + (uint32_t)(7 * N + c8), al);
                     }
                     tmem_ld_wait();
+                    // V = sum_q D_q 2^(-7q) in float-float, two columns at a time with the
+                    // packed instructions (each lane as the scalar float-float sum)
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        ff v{lv[0][c], 0.f};
+                    for (int c = 0; c < 8; c += 2) {
+                        float2 vh = make_float2(lv[0][c], lv[0][c + 1]), vl = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int q = 1; q < TC_NS; ++q) {
-                            const float x = __fmul_rn(lv[q][c], __uint_as_float((unsigned)(127 - 7 * q) << 23));
-                            v = ff_add(v, ff{x, 0.f});
+                            const float sc = __uint_as_float((unsigned)(127 - 7 * q) << 23);
+                            ff_add2(vh, vl, __fmul2_rn(make_float2(lv[q][c], lv[q][c + 1]), make_float2(sc, sc)),
+                                    make_float2(0.f, 0.f));
                         }
-                        if (!first) v = ff_add(ff{ah[c], al[c]}, v);
-                        ah[c] = v.hi;
-                        al[c] = v.lo;
+                        if (!first) {
+                            float2 xh = make_float2(ah[c], ah[c + 1]), xl = make_float2(al[c], al[c + 1]);
+                            ff_add2(xh, xl, vh, vl);
+                            vh = xh;
+                            vl = xl;
+                        }
+                        ah[c] = vh.x;
+                        ah[c + 1] = vh.y;
+                        al[c] = vl.x;
+                        al[c + 1] = vl.y;
                     }
                     if (last) {
                         if (valid) {
