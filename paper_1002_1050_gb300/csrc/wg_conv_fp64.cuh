@@ -141,11 +141,22 @@ __device__ __forceinline__ bool conv_fp64_item(const ConvArgs &A, const Tables &
     Angle ang[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
-        // a warp's chains are 32 x CPT consecutive angles: their 1e-30 crossings (and, with
-        // LMIN, their cuts) lie close together, so the warp starts its sum late when all
-        // its chains do and a cut tends to remove whole warps
-        jj[c] = chunk * NT * CPT + (tid >> 5) * (32 * CPT) + c * 32 + (tid & 31);
-        valid[c] = jj[c] < NB;
+        // a warp's chains lie close together in sin(beta), so their 1e-30 crossings (at
+        // l ~ m_sky / sin(beta); with LMIN, their cuts) do too: the warp starts its sum
+        // late when all its chains do, and a cut tends to remove whole warps.  With two
+        // chains and the sum in double a thread takes the angles j and N-1-j (pi - beta_j
+        // on a symmetric grid, the same sin(beta)), a warp 32 consecutive j of the grid's
+        // first half (measured 940.3 ms against 947.8 ms at the L = 4096 workload; the
+        // split-pipe form measured 618.9 against 615.5 ms and keeps the other map); else a
+        // warp takes 32 CPT consecutive angles.
+        if (CPT == 2 && !SUM_FF) {
+            const int jl = chunk * NT + tid;
+            jj[c] = c == 0 ? jl : NB - 1 - jl;
+            valid[c] = 2 * jl + c < NB;  // jl < N - 1 - jl for the second chain (the middle angle once)
+        } else {
+            jj[c] = chunk * NT * CPT + (tid >> 5) * (32 * CPT) + c * 32 + (tid & 31);
+            valid[c] = jj[c] < NB;
+        }
         ang[c] = make_angle(valid[c] ? A.beta[jj[c]] : 1.0);
         if (valid[c] && ang[c].bad) raise_status(T.status, WG_DEVERR_BETA);
     }
