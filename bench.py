@@ -943,7 +943,7 @@ def run_batched(args):
 
 # the dominant kernel as launched by wigner_conv_sum(form="fp64"); the committed DRAM
 # counters count only if they were taken on this same kernel
-FP64_KERNEL = "conv_fp64_kernel<256,2,128,false>, weights by TMA, 64 consecutive angles per warp"
+FP64_KERNEL = "conv_fp64_kernel<256,2,128,false>, weights by TMA, a thread's two chains at beta_j and pi - beta_j"
 
 
 def _profile_record():
