@@ -74,7 +74,7 @@ enum {
     WG_ERR_ALLOC = -3,       /* device allocation of the library's tables failed */
     WG_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up (reported by wigner_device_status) */
     WG_ERR_DEVICE = -5,      /* no usable sm_103 device / kernel image */
-    WG_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+    WG_ERR_UNSUPPORTED = -6  /* valid request this library version does not implement */
 };
 
 /* Optional counters filled by some calls (device pointer, may be NULL):

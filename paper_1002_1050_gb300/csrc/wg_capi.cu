@@ -276,7 +276,7 @@ const char *wigner_error_string(int code) {
         case WG_ERR_ALLOC: return "device allocation failed";
         case WG_ERR_TIMEOUT: return "bounded device wait timed out";
         case WG_ERR_DEVICE: return "unsupported device";
-        case WG_ERR_UNSUPPORTED: return "not supported by this build";
+        case WG_ERR_UNSUPPORTED: return "not supported by this library version";
         default: return "unknown error";
     }
 }

@@ -25,7 +25,7 @@ FORMS = {"fp64": WG_FP64, "fp32x": WG_FP32X, "fp64s": WG_FP64S}
 WG_LMAX = 32767
 
 _ERR = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "device allocation failed",
-        -4: "bounded device wait timed out", -5: "unsupported device", -6: "not supported by this build"}
+        -4: "bounded device wait timed out", -5: "unsupported device", -6: "not supported by this library version"}
 
 _lock = threading.Lock()
 _lib = None
