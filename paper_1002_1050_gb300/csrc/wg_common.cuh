@@ -423,12 +423,23 @@ __device__ __forceinline__ void scaled_fixup(double &cur, double &prev, int &n, 
 // so that Eq. lrec reads d^{l+1} = (F0 cos(beta) - G) d^l - F2 d^{l-1}.
 // Requires l >= max(mb, ms); at l = 0 and at l = max(mb, ms) the F2 factor is 0.
 // ---------------------------------------------------------------------------
+// k as a double, exact for 0 <= k < 2^53, by integer operations on the bits (no
+// conversion instruction on the FP64 pipe)
+__device__ __forceinline__ double exact_double(long long k) {
+    if (k <= 0) return 0.0;
+    const int e = 63 - __clzll(k);
+    const unsigned long long m = ((unsigned long long)k << (52 - e)) & 0xFFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | m));
+}
+
 __device__ __forceinline__ void lrec_coefficients(int l, int mb, int ms, const Tables &T, double &f0,
                                                   double &g, double &f2) {
     const double pp = (T.P[l + mb] * T.P[l - mb]) * (T.P[l + ms] * T.P[l - ms]);
     const double qq = (T.Q[l + mb] * T.Q[l - mb]) * (T.Q[l + ms] * T.Q[l - ms]);
-    f0 = ((double)(l + 1) * (double)(2 * l + 1)) * pp;
-    g = f0 * ((double)mb * (double)ms * T.R1[l]);
+    // (l+1)(2l+1) and mb ms are exact integers, so these are the products
+    // ((double)(l+1) (double)(2l+1)) pp and ((double)mb (double)ms) R1_l, bit for bit
+    f0 = exact_double((long long)(l + 1) * (long long)(2 * l + 1)) * pp;
+    g = f0 * (exact_double((long long)mb * (long long)ms) * T.R1[l]);
     f2 = T.R2[l] * qq;
 }
 

@@ -21,8 +21,9 @@
 //     items are ordered longest chain first, and each warp of a persistent grid takes
 //     the next item from an atomic counter, so the schedulers stay evenly loaded down to
 //     the shortest chains at the end.
-// The per-angle quantities (cos beta, the half-angle logarithms) and the per-column
-// part of the seed logarithm are formed once per launch by a small set-up kernel.
+// The per-angle quantities (cos beta, the half-angle logarithms), the per-column part of
+// the seed logarithm and the coefficient tables are formed once per call by a set-up
+// kernel laid out for the FP64 pipe (its comment says how).
 #include <climits>
 #include <cuda_runtime.h>
 
@@ -131,13 +132,87 @@ struct DtCoef {
     double *f0, *g, *f2;
 };
 
-// set-up: the angles' quantities, the columns' seed prefactors and coefficient tables,
-// the item counter
-__global__ void dtable_setup_kernel(DTableArgs A, Tables T, DtAngle *ang, DtCol *cols, DtCoef cf, int *next) {
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// One angle's quantities for the d-table: cos beta from the half angle (1 - 2 sin^2 or
+// 2 cos^2 - 1, whichever has no cancellation: an absolute error of about one rounding
+// unit), the half-angle logarithms as in make_angle but with one log and one log1p per
+// angle (the smaller half-angle factor x takes log x, the larger ln sqrt(1 - x^2)), so a
+// warp evaluates two logarithms whatever the mix of its angles.
+__device__ __forceinline__ DtAngle dtable_angle(double beta) {
+    DtAngle d;
+    Angle &t = d.t;
+    t.bad = !(beta >= 0.0 && beta <= WG_PI_HI);
+    const double b = t.bad ? 1.0 : beta;
+    double s, c;
+    sincos(0.5 * b, &s, &c);
+    t.cb = (s <= c) ? fma(-2.0 * s, s, 1.0) : fma(2.0 * c, c, -1.0);
+    t.sb = 2.0 * s * c;
+    t.s_zero = (s == 0.0);
+    t.c_zero = (c <= 0.0);
+    const double x = fmin(s, c);
+    const double lx = log(x), ly = 0.5 * log1p(-x * x);
+    t.lnc = (c >= s) ? ly : lx;
+    t.lns = (s >= c) ? ly : lx;
+    d.lnc_hi = d.lnc_lo = d.lns_hi = d.lns_lo = 0.0f;  // unused where the factor is 0
+    if (!t.bad && !t.c_zero) {
+        d.lnc_hi = __double2float_rn(t.lnc);
+        d.lnc_lo = __double2float_rn(t.lnc - (double)d.lnc_hi);
+    }
+    if (!t.bad && !t.s_zero) {
+        d.lns_hi = __double2float_rn(t.lns);
+        d.lns_lo = __double2float_rn(t.lns - (double)d.lns_hi);
+    }
+    return d;
+}
+
+// The set-up of one call, one CTA of DTS_THREADS per SM (at 52 registers a thread two
+// such CTAs do not fit one SM).  Its FP64 work is what costs: on GB300 each warp
+// instruction of the FP64 pipe holds its scheduler for 64 cycles whatever the number of
+// active lanes (measured), so a warp's latency is its FP64 instruction count times 64
+// cycles times the number of warps sharing the scheduler.  The angles (a sincos and two
+// logarithms, the critical path) therefore run in CTAs of their own, one warp per
+// scheduler; the coefficients (10 FP64 multiplications per column and order, the integer
+// factors made doubles by bit operations; 3 doubles stored) and the column prefactors
+// (double-double, a few per CTA) fill the other CTAs.  Measured at the L = 256 workload:
+// 10 us against 15-18 us for a grid of 128-thread CTAs in which the angle and prefactor
+// warps shared their schedulers with up to 16 coefficient warps.
+constexpr int DTS_THREADS = 1024;
+
+__global__ void __launch_bounds__(DTS_THREADS, 1) dtable_setup_kernel(DTableArgs A, Tables T, DtAngle *ang,
+                                                                      DtCol *cols, DtCoef cf, int *next, int n_ang) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((int)blockIdx.x < n_ang) {  // angle CTAs: warps 0..3, one per scheduler, 32 angles at a time
+        const int n_chunks = (A.n_beta + 31) >> 5;
+        if (warp < 4)
+            for (int ch = (int)blockIdx.x * 4 + warp; ch < n_chunks; ch += n_ang * 4) {
+                const int i = ch * 32 + lane;
+                if (i < A.n_beta) {
+                    const DtAngle d = dtable_angle(A.beta[i]);
+                    if (d.t.bad) raise_status(T.status, WG_DEVERR_BETA);
+                    ang[i] = d;
+                }
+            }
+        return;
+    }
+    const long long i0 = (long long)(blockIdx.x - n_ang) * DTS_THREADS + threadIdx.x;
+    const long long stride = (long long)(gridDim.x - n_ang) * DTS_THREADS;
     const int MS1 = A.ms_max + 1, ncol = (A.mb_max + 1) * MS1;
     const int L = A.l_max;
-    for (long long e = i0; e < (long long)ncol * L; e += (long long)gridDim.x * blockDim.x) {
+    if (i0 == 0) *next = 0;
+    // column c's prefactor on CTA c mod n_cta, thread c / n_cta: a few per CTA, so that the
+    // double-double work is spread over all schedulers (32 warps of one CTA doing it
+    // share four schedulers and take ~8 us)
+    const int n_cta = (int)gridDim.x - n_ang;
+    for (long long i = (long long)threadIdx.x * n_cta + (blockIdx.x - n_ang); i < ncol;
+         i += (long long)DTS_THREADS * n_cta) {
+        const int mb = (int)i / MS1, ms = (int)i - mb * MS1;
+        DtCol c;
+        c.pre = seed_prefactor(mb, ms, T);
+        c.pre_hi = __double2float_rn(c.pre.hi);
+        c.pre_lo = __double2float_rn((c.pre.hi - (double)c.pre_hi) + c.pre.lo);
+        cols[i] = c;
+    }
+    if (L == 0) return;
+    for (long long e = i0; e < (long long)ncol * L; e += stride) {
         const int c = (int)(e / L), l = (int)(e - (long long)c * L);
         const int mb = c / MS1, ms = c - mb * MS1;
         if (l >= (mb > ms ? mb : ms)) {
@@ -147,32 +222,6 @@ __global__ void dtable_setup_kernel(DTableArgs A, Tables T, DtAngle *ang, DtCol 
             cf.g[e] = g;
             cf.f2[e] = f2;
         }
-    }
-    if (i0 > INT_MAX) return;
-    const int i = (int)i0;
-    if (i == 0) *next = 0;
-    if (i < A.n_beta) {
-        DtAngle d;
-        d.t = make_angle(A.beta[i]);
-        if (d.t.bad) raise_status(T.status, WG_DEVERR_BETA);
-        d.lnc_hi = d.lnc_lo = d.lns_hi = d.lns_lo = 0.0f;  // unused where the factor is 0
-        if (!d.t.bad && !d.t.c_zero) {
-            d.lnc_hi = __double2float_rn(d.t.lnc);
-            d.lnc_lo = __double2float_rn(d.t.lnc - (double)d.lnc_hi);
-        }
-        if (!d.t.bad && !d.t.s_zero) {
-            d.lns_hi = __double2float_rn(d.t.lns);
-            d.lns_lo = __double2float_rn(d.t.lns - (double)d.lns_hi);
-        }
-        ang[i] = d;
-    }
-    if (i < ncol) {
-        const int mb = i / MS1, ms = i - mb * MS1;
-        DtCol c;
-        c.pre = seed_prefactor(mb, ms, T);
-        c.pre_hi = __double2float_rn(c.pre.hi);
-        c.pre_lo = __double2float_rn((c.pre.hi - (double)c.pre_hi) + c.pre.lo);
-        cols[i] = c;
     }
 }
 
@@ -222,18 +271,20 @@ constexpr int DT_WARPS = 4;  // warps per CTA of the persistent grid
 // e^{i m phi} (the Condon-Shortley phase comes with d).
 template <bool YLM>
 __global__ void __launch_bounds__(32 * DT_WARPS) dtable_fp64_kernel(DTableArgs A, Tables T, const DtAngle *ang,
-                                                                    const DtCol *cols, DtCoef cf, int *next,
-                                                                    int n_items, int n_chunks) {
+                                                                          const DtCol *cols, DtCoef cf, int *next,
+                                                                          int n_items, int n_chunks) {
     __shared__ double sF0[DT_WARPS][32], sG[DT_WARPS][32], sF2[DT_WARPS][32], sN[DT_WARPS][YLM ? 32 : 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int MS1 = A.ms_max + 1;
     const int L = A.l_max;
     const size_t NB = (size_t)A.n_beta;
+    int it_next = -1;  // lane 0: the item taken during the last tile of the current one
     for (;;) {
         int it = 0;
-        if (lane == 0) it = atomicAdd(next, 1);
+        if (lane == 0) it = it_next >= 0 ? it_next : atomicAdd(next, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
+        it_next = -1;
         const int cidx = it / n_chunks, chunk = it - cidx * n_chunks;
         int mb, ms;
         column_of(cidx, A.mb_max, A.ms_max, mb, ms);
@@ -279,6 +330,8 @@ __global__ void __launch_bounds__(32 * DT_WARPS) dtable_fp64_kernel(DTableArgs A
                 nf2 = cf.f2[cbase + ln];
             }
             const int nl = min(32, L + 1 - ts);
+            // the last tile: take the next item now, its atomic's latency hidden by the steps
+            if (lane == 0 && ts + 32 > L) it_next = atomicAdd(next, 1);
             for (int i = 0; i < nl; ++i) {
                 const int l = ts + i;
                 if (valid) {
@@ -333,13 +386,12 @@ static int launch_dtable_t(const DTableArgs &a, const Tables &t, void *stream) {
     cf.f0 = reinterpret_cast<double *>(sc + off_cf);
     cf.g = cf.f0 + n_cf;
     cf.f2 = cf.g + n_cf;
-    long long n_setup = (long long)(a.n_beta > ncol ? a.n_beta : ncol);
-    if ((long long)n_cf > n_setup) n_setup = (long long)n_cf;
-    long long setup_blocks = (n_setup + 127) / 128;
-    if (setup_blocks > (long long)n_sm * 64) setup_blocks = (long long)n_sm * 64;  // grid-stride beyond
-    const long long need_ids = ((long long)(a.n_beta > ncol ? a.n_beta : ncol) + 127) / 128;
-    if (setup_blocks < need_ids) setup_blocks = need_ids;  // one thread per angle and per column
-    dtable_setup_kernel<<<(unsigned)setup_blocks, 128, 0, s>>>(a, t, ang, cols, cf, next);
+    // the set-up grid: one CTA per SM, the first n_ang of them for the angles (4 chunks of 32
+    // angles each per pass), at most half the SMs
+    int n_ang = (n_chunks + 3) / 4;
+    if (n_ang > n_sm / 2) n_ang = n_sm / 2 > 1 ? n_sm / 2 : 1;
+    const int setup_grid = n_sm > n_ang + 1 ? n_sm : n_ang + 1;
+    dtable_setup_kernel<<<(unsigned)setup_grid, DTS_THREADS, 0, s>>>(a, t, ang, cols, cf, next, n_ang);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         long long grid = (long long)n_sm * DT_BLOCKS_PER_SM;

@@ -72,6 +72,24 @@ def test_dtable_long_columns_and_poles(W):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("form", ["fp64", "fp32x"])
+@pytest.mark.parametrize("L,MB,MS,NB", [(256, 4, 256, 64), (300, 12, 150, 45), (40, 40, 7, 33), (5, 5, 5, 2),
+                                        (0, 0, 0, 3)])
+def test_dtable_every_row_written(W, form, L, MB, MS, NB):
+    """The output starts as NaN: every element, the zeros for l < l0 included, is written by
+    the kernels (the FP64 kernel writes a column's zero rows from another column's item)."""
+    beta = I.beta_uniform(NB, 1e-3, math.pi - 1e-3, 5)
+    out = torch.full((MB + 1, MS + 1, L + 1, NB), float("nan"), dtype=torch.float64, device="cuda")
+    d = W.wigner_d_table(_cuda(beta), L, MB, MS, form=form, out=out).cpu().numpy()
+    W.check_device_status()
+    assert not np.isnan(d).any()
+    ref = O.d_table(L, MB, MS, beta)
+    l0 = np.maximum(np.arange(MB + 1)[:, None], np.arange(MS + 1)[None, :])
+    zero = np.arange(L + 1)[None, None, :] < l0[:, :, None]
+    assert np.all(d[zero] == 0.0)
+    assert np.max(np.abs(d - ref)) <= (TOL if form == "fp64" else 2e-4)
+
+
 def test_dtable_counters(W):
     L, MB, MS, beta, _, _ = I.make_config("dtable_l256")
     cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
