@@ -169,8 +169,8 @@ __device__ __forceinline__ DtAngle dtable_angle(double beta) {
 // instruction of the FP64 pipe holds its scheduler for 64 cycles whatever the number of
 // active lanes (measured), so a warp's latency is its FP64 instruction count times 64
 // cycles times the number of warps sharing the scheduler.  The angles (a sincos and two
-// logarithms, the critical path) therefore run in CTAs of their own, one warp per
-// scheduler; the coefficients (10 FP64 multiplications per column and order, the integer
+// logarithms: ~6k cycles for a warp alone on its scheduler, measured) therefore run in
+// CTAs of their own, one warp per scheduler; the coefficients (10 FP64 multiplications per column and order, the integer
 // factors made doubles by bit operations; 3 doubles stored) and the column prefactors
 // (double-double, a few per CTA) fill the other CTAs.  Measured at the L = 256 workload:
 // 10 us against 15-18 us for a grid of 128-thread CTAs in which the angle and prefactor
