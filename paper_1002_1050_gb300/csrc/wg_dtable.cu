@@ -305,8 +305,6 @@ __global__ void __launch_bounds__(32 * DT_WARPS) dtable_fp64_kernel(DTableArgs A
         bool plain = a.t.bad ? true : sd.plain;
 
         double *out = A.d_out + (size_t)col * (size_t)(L + 1) * NB;
-        if (valid)
-            for (int l = 0; l < l0; ++l) out[(size_t)l * NB + j] = 0.0;
         // the coefficients of a tile: lane i holds order ts + i, loaded one tile ahead
         const size_t cbase = (size_t)col * L;
         double nf0 = 0.0, ng = 0.0, nf2 = 0.0;
@@ -346,6 +344,19 @@ __global__ void __launch_bounds__(32 * DT_WARPS) dtable_fp64_kernel(DTableArgs A
                     if (!plain) scaled_fixup(cur, prev, n, plain);
                 }
             }
+        }
+        // The zeros of rows l < l0, written after the chain for another column: the item of
+        // (mb, ms), ms >= 1, zeroes column (mb, ms_max + 1 - ms) (a bijection of 1..ms_max),
+        // the item of (mb, 0) its own.  Items run longest chain first, and the columns with
+        // the longest chains have the fewest zero rows; paired this way the early items
+        // write the many zeros and the short items at the end of the queue few, instead of
+        // ending the kernel with stores while the FP64 pipe idles.
+        {
+            const int msz = ms == 0 ? 0 : A.ms_max + 1 - ms;
+            const int zn = mb > msz ? mb : msz;
+            double *z = A.d_out + (size_t)(mb * MS1 + msz) * (size_t)(L + 1) * NB + j;
+            if (valid)
+                for (int l = 0; l < zn; ++l) z[(size_t)l * NB] = 0.0;
         }
         if (A.counters && lane == 0) {
             const int nvalid = min(32, A.n_beta - chunk * 32);
