@@ -86,10 +86,17 @@ typedef unsigned long long wg_counter;
 /* ---------------------------------------------------------------------------
  * wigner_d_table -- the full table (Sec. 3.2 l-recursion, Eqs. lrec, ini1-ini2, logstart).
  *   d_out[mb][ms][l][j] = d^l_{mb,ms}(beta_j),  shape (mb_max+1, ms_max+1, l_max+1, n_beta),
- *   float64, 8-byte aligned; entries with l < max(mb, ms) are written as 0.
- *   form: WG_FP64 or WG_FP32X (the stored values are double in both cases).
+ *   float64, 8-byte aligned; entries with l < max(mb, ms) are written as 0 (every element
+ *   of d_out is written).
+ *   form: WG_FP64 (WG_FP64S is taken as WG_FP64) or WG_FP32X (the stored values are double
+ *   in both cases).
  *   counters: optional, see above.
- * Errors: WG_ERR_ARG for bad orders/sizes/pointers; WG_ERR_CUDA on launch failure.
+ *   Per call the library takes stream-ordered scratch from its own memory pool (the FP64
+ *   form: 56 B per angle, 24 B per column and order, 24 B per column) and returns it on
+ *   the same stream.  An angle outside [0, pi] makes its entries NaN and sets the device
+ *   status (wigner_device_status returns WG_ERR_ARG).
+ * Errors: WG_ERR_ARG for bad orders/sizes/pointers; WG_ERR_ALLOC when the scratch cannot
+ * be allocated; WG_ERR_CUDA on launch failure.
  * ------------------------------------------------------------------------- */
 int wigner_d_table(int l_max, int mb_max, int ms_max, int n_beta, const double *beta,
                    wg_form form, double *d_out, wg_counter *counters, void *stream);
